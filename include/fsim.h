@@ -1,0 +1,194 @@
+/*
+ * fsim.h -- C-ABI of libfsim, a GB300 (sm_103a) implementation of the
+ * McMurchie-Davidson restricted Hartree-Fock hot path of arXiv 2510.24968
+ * ("FSIM: A Pedagogical and Extensible HPC Framework for the Hartree-Fock
+ * Method").  The calls follow the paper's statement of the problem: a molecule
+ * and a basis go in (Sec. 3.1), the two-electron part of the Fock matrix
+ * F[D] = H + J - K/2 is built from a density (Sec. 2.2, Eq. fock; Sec. 3.2),
+ * and the SCF of Sec. 3.2 returns the total energy.
+ *
+ * Conventions (all calls):
+ *  - Return FSIM_OK (0) on success, a negative FSIM_E* code otherwise; the
+ *    message of the last failure on the calling thread is fsim_last_error().
+ *  - Units: bohr, hartree.  Basis functions are contracted CARTESIAN Gaussians
+ *    (s, p, d); inside a shell the components are ordered x, y, z (p) and
+ *    xx, xy, xz, yy, yz, zz (d).  Matrices are nbf x nbf, row-major, FP64, with
+ *    the basis functions in the order of the shells passed to
+ *    fsim_basis_create.
+ *  - The library copies every input it needs; arrays passed in stay owned by
+ *    the caller and may be freed after the call returns.  Outputs are written
+ *    into caller-owned arrays of the stated size.
+ *  - Work runs on the CUDA device that is current when fsim_basis_create is
+ *    called; the basis keeps device buffers until fsim_basis_destroy.
+ *  - A basis handle is not thread-safe: calls on one handle must not overlap.
+ */
+#ifndef FSIM_H
+#define FSIM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FSIM_OK 0
+#define FSIM_EINVAL (-1)          /* bad argument (null pointer, size, l > 2, ...) */
+#define FSIM_ECUDA (-2)           /* a CUDA runtime / library call failed */
+#define FSIM_ENOCONV (-3)         /* SCF hit max_iter; the result struct is still filled */
+#define FSIM_EILLCOND (-4)        /* overlap matrix (near) singular: min eigenvalue < 1e-10 */
+#define FSIM_EDEVICE_TIMEOUT (-5) /* a bounded device-side wait gave up */
+#define FSIM_ENOMEM (-6)          /* device allocation failed */
+
+#define FSIM_FP64 0   /* every step in FP64 */
+#define FSIM_MIXED 1  /* FP32 Hermite integrals + contraction, FP64 J/K accumulation, FP64 Boys above boys_fp64_T */
+
+#define FSIM_PTR_HOST 0
+#define FSIM_PTR_DEVICE 1
+
+#define FSIM_GUESS_CORE 0     /* diagonalise H_core in the orthogonal basis (Sec. 3.2, step 1) */
+#define FSIM_GUESS_DENSITY 1  /* caller-supplied density fsim_scf_opts.D0 */
+
+typedef struct fsim_basis fsim_basis; /* opaque, owned by the library */
+
+typedef struct {
+  int Z;          /* nuclear charge (electrons counted from it) */
+  double xyz[3];  /* bohr */
+} fsim_atom;
+
+typedef struct {
+  int atom;             /* index into the atom array */
+  int l;                /* 0, 1 or 2 */
+  int nprim;            /* 1 .. 4 primitives */
+  const double* alpha;  /* nprim exponents, > 0 */
+  const double* coef;   /* nprim raw contraction coefficients d_k */
+} fsim_shell_desc;
+
+/*
+ * Build a contracted Cartesian basis (Sec. 2.1.1, 2.4).  Each primitive is
+ * normalised per Cartesian component, N = (2a/pi)^{3/4} (4a)^{l/2} /
+ * sqrt((2i-1)!!(2j-1)!!(2k-1)!!), and each contracted function is rescaled so
+ * that S_mumu = 1.  Builds the shell-pair data (Gaussian product theorem,
+ * Sec. 2.1.2; Hermite coefficients E^{ij}_t of Eqs. recurrence-A/B, collapsed
+ * per Eq. E-tuv) on the device.  *out receives a new handle.
+ * Errors: FSIM_EINVAL for bad sizes or l > 2 or nprim outside 1..4,
+ * FSIM_ECUDA / FSIM_ENOMEM from the device.
+ */
+int fsim_basis_create(const fsim_atom* atoms, int natom, const fsim_shell_desc* shells, int nshell,
+                      fsim_basis** out);
+void fsim_basis_destroy(fsim_basis* b);
+int fsim_basis_nbf(const fsim_basis* b);
+int fsim_basis_nshell(const fsim_basis* b);
+/* Number of unique shell pairs in each of the six pair classes ss, ps, pp, ds, dp, dd. */
+int fsim_basis_pair_counts(const fsim_basis* b, int counts[6]);
+
+/*
+ * Nuclear repulsion sum_{A<B} Z_A Z_B / R_AB (added to E_elec, Sec. 3.2).
+ */
+int fsim_enuc(const fsim_basis* b, double* e_nuc);
+
+/*
+ * One-electron matrices (Sec. 2.3.1 Eq. s-overall, Sec. 2.3.2 Eq. Tab-final,
+ * Sec. 2.3.3 Eq. Vab-final); which = 0 overlap S, 1 kinetic T, 2 nuclear
+ * attraction V.  out: nbf*nbf, host or device pointer per ptr_mode.  stream:
+ * cudaStream_t or NULL.
+ */
+int fsim_onee(fsim_basis* b, int which, double* out, int ptr_mode, void* stream);
+
+/*
+ * Schwarz bounds (not defined in the paper; this library's reading):
+ * Q_ab = sqrt(max_{mu in a, nu in b} |(mu nu|mu nu)|) for every shell pair,
+ * evaluated in FP64 with the ERI kernels on the diagonal quartets.  Also sorts
+ * each pair class by Q (descending), which the Fock build uses for screening.
+ * Q: nshell*nshell host array (may be NULL to only prepare the screening).
+ */
+int fsim_schwarz(fsim_basis* b, double* Q);
+
+typedef struct {
+  double schwarz_tau;  /* skip unique quartets with Q_ab Q_cd < tau; 0 = no screening */
+  int precision;       /* FSIM_FP64 or FSIM_MIXED */
+  double boys_fp64_T;  /* mixed path: Boys in FP64 for T above this (fixed at 30; other values are rejected) */
+  int ptr_mode;        /* FSIM_PTR_HOST or FSIM_PTR_DEVICE for D, J, K */
+  void* stream;        /* cudaStream_t; NULL = legacy default stream */
+  int shard;           /* this shard's index in [0, nshards): bra pairs i with i % nshards == shard */
+  int nshards;         /* 1 = whole build */
+} fsim_fock_opts;
+
+/* Fills the defaults: tau 1e-10, FP64, boys_fp64_T 30, host pointers, NULL stream, 1 shard. */
+void fsim_fock_opts_default(fsim_fock_opts* o);
+
+/*
+ * Coulomb and exchange matrices of a symmetric density (Sec. 2.2, Eq. fock):
+ *   J_mu,nu = sum_{la,si} D_la,si (mu nu|la si),  K_mu,nu = sum_{la,si} D_la,si (mu la|nu si),
+ * so that G = J - K/2.  ERIs by the McMurchie-Davidson scheme (Eq. twoe-final)
+ * over each shell quartet unique under the 8-fold permutational symmetry that
+ * survives Schwarz screening, digested directly into J and K.  D, J, K:
+ * nbf*nbf row-major FP64, host or device per opts->ptr_mode (J and K are
+ * overwritten).  With nshards > 1 only this shard's bra pairs contribute (the
+ * caller sums J and K over shards).  Calls fsim_schwarz first if it has not run.
+ * Errors: FSIM_EINVAL (null pointers, bad options), FSIM_ECUDA.
+ */
+int fsim_fock_build(fsim_basis* b, const double* D, double* J, double* K, const fsim_fock_opts* opts);
+
+/* Unique shell quartets the last fsim_fock_build evaluated (after screening). */
+long long fsim_last_quartet_count(const fsim_basis* b);
+
+/*
+ * Contracted ERI blocks (mu nu|la si) for explicit shell quartets, by the same
+ * kernels as the Fock build (debug / parity).  quartets: 4*n shell indices
+ * (a,b,c,d); out: concatenated blocks, each na*nb*nc*nd in (a,b,c,d)
+ * row-major order; host pointers; precision FSIM_FP64 or FSIM_MIXED.
+ */
+int fsim_eri_quartets(fsim_basis* b, int n, const int* quartets, double* out, int precision);
+
+/*
+ * All ERIs g[mu][nu][la][si] (nbf <= 64, nbf^4 host doubles).  Debug / parity.
+ */
+int fsim_eri_dump(fsim_basis* b, double* g, int precision);
+
+typedef struct {
+  int nelec;            /* electrons (even) */
+  int max_iter;         /* e.g. 100 */
+  double conv_dE;       /* |E_n - E_{n-1}| threshold, e.g. 1e-10 */
+  double conv_dD;       /* rms(D_n - D_{n-1}) threshold, e.g. 1e-7 */
+  int diis_size;        /* stored Fock/error pairs (Sec. 3.2.1: 6-8); 0 disables DIIS */
+  int guess;            /* FSIM_GUESS_CORE or FSIM_GUESS_DENSITY */
+  const double* D0;     /* host nbf*nbf initial density for FSIM_GUESS_DENSITY */
+  fsim_fock_opts fock;  /* screening, precision and stream of the Fock builds */
+  int final_fp64;       /* FSIM_MIXED: after mixed convergence, finish with FP64 Fock builds */
+  int incremental;      /* build G(D_n) as G(D_{n-1}) + G(D_n - D_{n-1}) */
+} fsim_scf_opts;
+
+void fsim_scf_opts_default(fsim_scf_opts* o);
+
+typedef struct {
+  double e_total, e_elec, e_nuc;
+  int iters;
+  int converged;
+  int guess_fallback;   /* 1 when a supplied guess failed its trace/idempotency check and core-H was used */
+  double* D_out;        /* optional caller-owned nbf*nbf host array: final density */
+  double* e_hist;       /* optional caller-owned max_iter array: total energy after each Fock build */
+  double* t_hist;       /* optional caller-owned max_iter array: seconds since the call started */
+  double time_s;        /* wall time of the SCF loop */
+  double min_s_eig;     /* smallest eigenvalue of S */
+  long long quartets;   /* unique quartets evaluated over all Fock builds */
+  int fp64_builds;      /* Fock builds done in FP64 */
+  int mixed_builds;     /* Fock builds done in mixed precision */
+} fsim_scf_result;
+
+/*
+ * Restricted Hartree-Fock SCF (Sec. 3.2): core-Hamiltonian (or supplied)
+ * guess, symmetric orthogonalisation X = U s^{-1/2} U^T, then per iteration
+ * G(D) by fsim_fock_build, F = H + G, E_elec = 1/2 Tr[D (H + F)], DIIS
+ * extrapolation (Sec. 3.2.1, Algorithm 1; error F D S - S D F), F' = X^T F X,
+ * diagonalisation, C = X C', D = 2 C_occ C_occ^T.  Converged when
+ * |dE| < conv_dE and rms(dD) < conv_dD.  All linear algebra in FP64 on the
+ * device.  Returns FSIM_ENOCONV (result filled) at max_iter, FSIM_EILLCOND if
+ * min eig(S) < 1e-10.
+ */
+int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* fsim_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FSIM_H */

@@ -1,0 +1,355 @@
+// Shell-quartet kernels of the McMurchie-Davidson ERI engine (paper Sec. 2.3.4,
+// Eq. twoe-final; contracted form Eq. eri-tensor-contracted of Sec. 2.5),
+// fused with Schwarz screening and J/K digestion (Eq. fock).
+//
+// For a quartet (ab|cd) of bra pair class (LA,LB) and ket pair class (LC,LD),
+// each primitive quartet contributes
+//   [ab|cd] = 2 pi^{5/2} / (p q sqrt(p+q))
+//             sum_{tuv} sum_{tau nu phi} (-1)^{tau+nu+phi} E^{ab}_{tuv} E^{cd}_{tau nu phi}
+//             R^0_{t+tau, u+nu, v+phi}(alpha = pq/(p+q), P - Q)
+// with R^0 from the recursion of Eq. R-recursion seeded by the Boys function.
+// Evaluation order (per thread = one shell quartet, ket components in chunks
+// of CS so that the per-thread arrays stay in registers):
+//   for each bra primitive pair b:
+//     W[h][c] = sum_k sum_{h' in nz(c)} sign(h') E^{cd,k}_{h'} R^{bk}[h + h']   (ket transform)
+//     out[a][c] += sum_{h in nz(a)} E^{ab,b}_h W[h][c]                            (bra transform)
+// Pair data already folds the contraction coefficients, the Cartesian
+// normalisation and sqrt(2) pi^{5/4} / p into E, so only 1/sqrt(p+q) remains
+// per primitive quartet (folded into the Boys source terms).
+#pragma once
+#include <cuda_runtime.h>
+#include <type_traits>
+
+#include "boys.cuh"
+#include "md_tables.cuh"
+
+namespace fsim {
+
+constexpr int kJKThreads = 128;
+
+// One pair class on the device.  Pairs are sorted by Schwarz bound, descending.
+// Primitive-pair data is SoA: value (field f, primitive pair k, pair j) at
+// pd[(f * ppmax + k) * n + j]; fields: 0 = p, 1..3 = P, 4.. = E non-zeros.
+template <typename Real>
+struct PairView {
+  int n;
+  int ppmax;
+  const int4* __restrict__ idx;  // (ao_a, ao_b, shell_a, shell_b)
+  const int* __restrict__ npp;   // primitive pairs of each pair
+  const Real* __restrict__ pd;
+};
+
+template <typename Real>
+struct JKParams {
+  PairView<Real> bra, ket;
+  const int* __restrict__ tile_prefix;  // [nbra + 1] cumulative ket tiles per bra
+  const int* __restrict__ ket_count;    // [nbra] screened ket prefix length per bra
+  int nitems;
+  int same;                             // bra class == ket class
+  int psplit;                           // bra primitive pairs split over this many threads
+  int N;
+  const Real* __restrict__ D;           // density, N x N, in the working precision
+  double* J;                            // accumulators (FP64), N x N
+  double* K;
+  const Real* __restrict__ boys;
+};
+
+// Hermite Coulomb integrals R^0_{tuv} for t+u+v <= L, in place (Eq. R-recursion):
+// level n is derived from level n+1 processing total orders s = L-n .. 1
+// (higher first) so that lower orders still hold level n+1 when read.
+template <typename Real, int L>
+__device__ __forceinline__ void hermite_R(Real (&R)[nherm(L)], const Real (&src)[L + 1], Real X, Real Y,
+                                          Real Z) {
+  R[0] = src[L];
+  static_for<L>([&](auto I) {
+    constexpr int n = L - 1 - decltype(I)::value;
+    static_for<L - n>([&](auto S) {
+      constexpr int s = L - n - decltype(S)::value;
+      static_for<s + 1>([&](auto Tt) {
+        constexpr int t = decltype(Tt)::value;
+        static_for<s - t + 1>([&](auto Uu) {
+          constexpr int u = decltype(Uu)::value;
+          constexpr int v = s - t - u;
+          if constexpr (t > 0) {
+            if constexpr (t > 1)
+              R[hidx(t, u, v)] = X * R[hidx(t - 1, u, v)] + Real(t - 1) * R[hidx(t - 2, u, v)];
+            else
+              R[hidx(t, u, v)] = X * R[hidx(t - 1, u, v)];
+          } else if constexpr (u > 0) {
+            if constexpr (u > 1)
+              R[hidx(t, u, v)] = Y * R[hidx(t, u - 1, v)] + Real(u - 1) * R[hidx(t, u - 2, v)];
+            else
+              R[hidx(t, u, v)] = Y * R[hidx(t, u - 1, v)];
+          } else {
+            if constexpr (v > 1)
+              R[hidx(t, u, v)] = Z * R[hidx(t, u, v - 1)] + Real(v - 1) * R[hidx(t, u, v - 2)];
+            else
+              R[hidx(t, u, v)] = Z * R[hidx(t, u, v - 1)];
+          }
+        });
+      });
+    });
+    R[0] = src[n];
+  });
+}
+
+template <typename Real>
+__device__ __forceinline__ Real rsqrt_r(Real x);
+template <>
+__device__ __forceinline__ double rsqrt_r<double>(double x) { return rsqrt(x); }
+template <>
+__device__ __forceinline__ float rsqrt_r<float>(float x) { return rsqrtf(x); }
+
+// Chunk bookkeeping for the ket side.
+template <class KC, int CS>
+struct KetChunks {
+  static constexpr int NCH = KC::NC / CS;
+  static_assert(KC::NC % CS == 0, "chunk must divide the ket component count");
+  __host__ __device__ static constexpr int nnz_of(int ch) { return KC::off((ch + 1) * CS) - KC::off(ch * CS); }
+  __host__ __device__ static constexpr int max_nnz() {
+    int m = 0;
+    for (int ch = 0; ch < NCH; ++ch) m = nnz_of(ch) > m ? nnz_of(ch) : m;
+    return m;
+  }
+};
+
+// Contracted quartet block for one ket chunk: out[a][cs] for all bra components a
+// and ket components c = CH*CS + cs.  Bra data: accessor bra(field, pp).
+template <typename Real, int LA, int LB, int LC, int LD, int CS, int CH, class BraAt>
+__device__ __forceinline__ void quartet_chunk(Real (&out)[PairCls<LA, LB>::NC][CS], const BraAt& bra, int nppb,
+                                              int b0, int bstep, const PairView<Real>& ket, int j, int nppk,
+                                              const Real* __restrict__ boys) {
+  using BC = PairCls<LA, LB>;
+  using KC = PairCls<LC, LD>;
+  using KCh = KetChunks<KC, CS>;
+  constexpr int L = LA + LB + LC + LD;
+  constexpr int NH = nherm(L);
+  constexpr int NH1 = BC::NH;
+  constexpr int c0 = CH * CS;
+  constexpr int nzoff = KC::off(c0);
+  constexpr int NZ = KCh::nnz_of(CH);
+#pragma unroll
+  for (int a = 0; a < BC::NC; ++a)
+#pragma unroll
+    for (int cs = 0; cs < CS; ++cs) out[a][cs] = Real(0);
+
+  const size_t kstride = (size_t)ket.ppmax * ket.n;
+  for (int b = b0; b < nppb; b += bstep) {
+    const Real p = bra(0, b), Px = bra(1, b), Py = bra(2, b), Pz = bra(3, b);
+    Real W[NH1][CS];
+#pragma unroll
+    for (int h = 0; h < NH1; ++h)
+#pragma unroll
+      for (int cs = 0; cs < CS; ++cs) W[h][cs] = Real(0);
+
+    for (int k = 0; k < nppk; ++k) {
+      const Real* kp = ket.pd + (size_t)k * ket.n + j;
+      const Real q = __ldg(kp), Qx = __ldg(kp + kstride), Qy = __ldg(kp + 2 * kstride),
+                 Qz = __ldg(kp + 3 * kstride);
+      Real Ek[NZ];
+#pragma unroll
+      for (int z = 0; z < NZ; ++z) Ek[z] = __ldg(kp + (size_t)(4 + nzoff + z) * kstride);
+      const Real s = p + q;
+      const Real rs = rsqrt_r<Real>(s);
+      const Real al = p * q * (rs * rs);
+      const Real X = Px - Qx, Y = Py - Qy, Z = Pz - Qz;
+      const Real T = al * (X * X + Y * Y + Z * Z);
+      Real F[L + 1];
+      Boys<Real>::template eval<L>(T, F, boys);
+      Real src[L + 1];
+      Real fac = rs;
+      const Real m2a = Real(-2) * al;
+#pragma unroll
+      for (int n = 0; n <= L; ++n) {
+        src[n] = fac * F[n];
+        fac *= m2a;
+      }
+      Real R[NH];
+      hermite_R<Real, L>(R, src, X, Y, Z);
+      // ket transform over the non-zeros of each ket component of this chunk
+      static_for<CS>([&](auto Cs) {
+        constexpr int cs = decltype(Cs)::value;
+        constexpr int c = c0 + cs;
+        constexpr int zb = KC::off(c) - nzoff;
+        static_for<KC::nnz(c)>([&](auto Kk) {
+          constexpr int kk = decltype(Kk)::value;
+          constexpr int tau = KC::nz_t(c, kk), nu = KC::nz_u(c, kk), phi = KC::nz_v(c, kk);
+          const Real e = ((tau + nu + phi) & 1) ? -Ek[zb + kk] : Ek[zb + kk];
+          static_for<NH1>([&](auto Hh) {
+            constexpr int h = decltype(Hh)::value;
+            constexpr int hr = hidx(herm_t(h) + tau, herm_u(h) + nu, herm_v(h) + phi);
+            W[h][cs] = fma(e, R[hr], W[h][cs]);
+          });
+        });
+      });
+    }
+    // bra transform with this bra primitive pair's E non-zeros
+    static_for<BC::NC>([&](auto Aa) {
+      constexpr int a = decltype(Aa)::value;
+      static_for<BC::nnz(a)>([&](auto Kk) {
+        constexpr int kk = decltype(Kk)::value;
+        constexpr int h = hidx(BC::nz_t(a, kk), BC::nz_u(a, kk), BC::nz_v(a, kk));
+        const Real e = bra(4 + BC::off(a) + kk, b);
+#pragma unroll
+        for (int cs = 0; cs < CS; ++cs) out[a][cs] = fma(e, W[h][cs], out[a][cs]);
+      });
+    });
+  }
+}
+
+// Binary search: largest i in [0, n) with prefix[i] <= item.
+__device__ __forceinline__ int find_bra(const int* __restrict__ prefix, int n, int item) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(prefix + mid) <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Fused ERI + J/K kernel.  One CTA = one (bra pair, tile of kets); thread =
+// (ket, bra-primitive subset).  Accumulates J_acc, K_acc with the 8-fold
+// degeneracy factor; the caller symmetrises J = (J_acc + J_acc^T)/4 and
+// K = (K_acc + K_acc^T)/8.
+template <typename Real, int LA, int LB, int LC, int LD, int CS>
+__global__ void __launch_bounds__(kJKThreads) jk_kernel(JKParams<Real> P) {
+  using BC = PairCls<LA, LB>;
+  using KC = PairCls<LC, LD>;
+  constexpr int NFB = 4 + BC::NNZ;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sDab = reinterpret_cast<double*>(smem_raw);   // D_{mu nu} of the bra block
+  double* sJab = sDab + BC::NC;                         // J_acc partial of the bra block
+  Real* sbra = reinterpret_cast<Real*>(sJab + BC::NC);  // bra primitive data [pp][field]
+
+  const int item = blockIdx.x;
+  if (item >= P.nitems) return;
+  const int i = find_bra(P.tile_prefix, P.bra.n, item);
+  const int tile = item - __ldg(P.tile_prefix + i);
+  const int4 bi = P.bra.idx[i];
+  const int nppb = P.bra.npp[i];
+  const int N = P.N;
+
+  for (int x = threadIdx.x; x < nppb * NFB; x += blockDim.x) {
+    const int pp = x / NFB, f = x % NFB;
+    sbra[x] = P.bra.pd[((size_t)f * P.bra.ppmax + pp) * P.bra.n + i];
+  }
+  for (int x = threadIdx.x; x < BC::NC; x += blockDim.x) {
+    sDab[x] = (double)P.D[(size_t)(bi.x + x / BC::NB) * N + bi.y + x % BC::NB];
+    sJab[x] = 0.0;
+  }
+  __syncthreads();
+
+  const int ps = P.psplit;
+  const int tq = blockDim.x / ps;
+  const int q = threadIdx.x / ps, bs = threadIdx.x % ps;
+  const int j = tile * tq + q;
+  Real jb[BC::NC];  // this thread's part of J_acc for the bra block
+#pragma unroll
+  for (int a = 0; a < BC::NC; ++a) jb[a] = Real(0);
+  if (q < tq && j < __ldg(P.ket_count + i)) {
+    const int4 ki = P.ket.idx[j];
+    const int nppk = P.ket.npp[j];
+    const Real deg = Real((bi.z == bi.w ? 1 : 2) * (ki.z == ki.w ? 1 : 2) * ((P.same && i == j) ? 1 : 2));
+    auto bra = [&](int f, int pp) -> Real { return sbra[pp * NFB + f]; };
+    static_for<KetChunks<KC, CS>::NCH>([&](auto Ch) {
+      constexpr int ch = decltype(Ch)::value;
+      Real out[BC::NC][CS];
+      quartet_chunk<Real, LA, LB, LC, LD, CS, ch>(out, bra, nppb, bs, ps, P.ket, j, nppk, P.boys);
+      // digestion (Eq. fock) of this chunk
+#pragma unroll
+      for (int cs = 0; cs < CS; ++cs) {
+        const int c = ch * CS + cs;
+        const int lam = ki.x + c / KC::NB, sig = ki.y + c % KC::NB;
+        // J_ket[la si] += sum_a D_ab v ; J_bra[a] += D_{la si} v
+        const Real Dls = P.D[(size_t)lam * N + sig];
+        Real jk = Real(0);
+#pragma unroll
+        for (int a = 0; a < BC::NC; ++a) {
+          const Real v = deg * out[a][cs];
+          jk = fma((Real)sDab[a], v, jk);
+          jb[a] = fma(Dls, v, jb[a]);
+        }
+        atomicAdd(&P.J[(size_t)lam * N + sig], (double)jk);
+        // K: (mu la) += D_nu si v ; (nu si) += D_mu la v ; (mu si) += D_nu la v ; (nu la) += D_mu si v
+#pragma unroll
+        for (int ia = 0; ia < BC::NA; ++ia) {
+          const int mu = bi.x + ia;
+          Real k1 = Real(0), k3 = Real(0);
+#pragma unroll
+          for (int ib = 0; ib < BC::NB; ++ib) {
+            const int nu = bi.y + ib;
+            const Real v = deg * out[ia * BC::NB + ib][cs];
+            k1 = fma(P.D[(size_t)nu * N + sig], v, k1);
+            k3 = fma(P.D[(size_t)nu * N + lam], v, k3);
+          }
+          atomicAdd(&P.K[(size_t)mu * N + lam], (double)k1);
+          atomicAdd(&P.K[(size_t)mu * N + sig], (double)k3);
+        }
+#pragma unroll
+        for (int ib = 0; ib < BC::NB; ++ib) {
+          const int nu = bi.y + ib;
+          Real k2 = Real(0), k4 = Real(0);
+#pragma unroll
+          for (int ia = 0; ia < BC::NA; ++ia) {
+            const int mu = bi.x + ia;
+            const Real v = deg * out[ia * BC::NB + ib][cs];
+            k2 = fma(P.D[(size_t)mu * N + lam], v, k2);
+            k4 = fma(P.D[(size_t)mu * N + sig], v, k4);
+          }
+          atomicAdd(&P.K[(size_t)nu * N + sig], (double)k2);
+          atomicAdd(&P.K[(size_t)nu * N + lam], (double)k4);
+        }
+      }
+    });
+  }
+  // J_bra: warp reduction (every lane takes part, idle lanes hold zeros), one
+  // shared-memory add per warp and element, one global add per CTA and element
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int a = 0; a < BC::NC; ++a) {
+    Real v = jb[a];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) atomicAdd(&sJab[a], (double)v);
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < BC::NC; x += blockDim.x)
+    atomicAdd(&P.J[(size_t)(bi.x + x / BC::NB) * N + bi.y + x % BC::NB], sJab[x]);
+}
+
+// Explicit list of (bra, ket) pair indices; writes each contracted block
+// out[item * NCb * NCk + a * NCk + c] in FP64.  Used for the Schwarz
+// diagonal, the debug ERI dump and sampled parity checks.
+template <typename Real>
+struct ListParams {
+  PairView<Real> bra, ket;
+  const int2* __restrict__ items;
+  int nitems;
+  double* out;
+  const Real* __restrict__ boys;
+};
+
+template <typename Real, int LA, int LB, int LC, int LD, int CS>
+__global__ void __launch_bounds__(kJKThreads) list_kernel(ListParams<Real> P) {
+  using BC = PairCls<LA, LB>;
+  using KC = PairCls<LC, LD>;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= P.nitems) return;
+  const int2 it = P.items[t];
+  const int i = it.x, j = it.y;
+  const int nppb = P.bra.npp[i], nppk = P.ket.npp[j];
+  const size_t bstride = (size_t)P.bra.ppmax * P.bra.n;
+  auto bra = [&](int f, int pp) -> Real { return __ldg(P.bra.pd + (size_t)f * bstride + (size_t)pp * P.bra.n + i); };
+  double* o = P.out + (size_t)t * BC::NC * KC::NC;
+  static_for<KetChunks<KC, CS>::NCH>([&](auto Ch) {
+    constexpr int ch = decltype(Ch)::value;
+    Real out[BC::NC][CS];
+    quartet_chunk<Real, LA, LB, LC, LD, CS, ch>(out, bra, nppb, 0, 1, P.ket, j, nppk, P.boys);
+#pragma unroll
+    for (int a = 0; a < BC::NC; ++a)
+#pragma unroll
+      for (int cs = 0; cs < CS; ++cs) o[a * KC::NC + ch * CS + cs] = (double)out[a][cs];
+  });
+}
+
+}  // namespace fsim

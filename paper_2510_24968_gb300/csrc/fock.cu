@@ -1,0 +1,440 @@
+// Fock build J, K from D (paper Sec. 2.2 Eq. fock; Sec. 3.2 step "Build the
+// G-Matrix"), debug ERI access, and the screened work plans.
+//
+// Work decomposition: for each class pair (bra class X >= ket class Y) and
+// each bra pair i (pairs of a class sorted by Schwarz bound Q, descending),
+// the kets that survive Q_i Q_j >= tau form a prefix of class Y; with X == Y
+// the prefix is cut at j <= i so each unique quartet appears once.  A work
+// item is (bra, tile of consecutive kets); one CTA per item.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "coop.cuh"
+#include "fsim_internal.h"
+
+namespace fsim {
+
+extern template cudaError_t launch_coop<double>(const CoopParams<double>&, int, cudaStream_t);
+extern template cudaError_t launch_coop<float>(const CoopParams<float>&, int, cudaStream_t);
+
+int ensure_schwarz(fsim_basis* b);
+
+template <typename Real, int X, int Y>
+static cudaError_t launch_jk_if(const JKParams<Real>& p, cudaStream_t s) {
+  constexpr int L = pair_cls_la(X) + pair_cls_lb(X) + pair_cls_la(Y) + pair_cls_lb(Y);
+  if constexpr (std::is_same<Real, double>::value && L >= kCoopMinL64) {
+    return cudaErrorInvalidValue;  // these run on the cooperative kernel
+  } else {
+    return launch_jk<Real, X, Y>(p, s);
+  }
+}
+
+template <typename Real>
+static cudaError_t dispatch_jk(int X, int Y, const JKParams<Real>& p, cudaStream_t s) {
+  switch (X * 8 + Y) {
+    case 0: return launch_jk_if<Real, 0, 0>(p, s);
+    case 8: return launch_jk_if<Real, 1, 0>(p, s);
+    case 9: return launch_jk_if<Real, 1, 1>(p, s);
+    case 16: return launch_jk_if<Real, 2, 0>(p, s);
+    case 17: return launch_jk_if<Real, 2, 1>(p, s);
+    case 18: return launch_jk_if<Real, 2, 2>(p, s);
+    case 24: return launch_jk_if<Real, 3, 0>(p, s);
+    case 25: return launch_jk_if<Real, 3, 1>(p, s);
+    case 26: return launch_jk_if<Real, 3, 2>(p, s);
+    case 27: return launch_jk_if<Real, 3, 3>(p, s);
+    case 32: return launch_jk_if<Real, 4, 0>(p, s);
+    case 33: return launch_jk_if<Real, 4, 1>(p, s);
+    case 34: return launch_jk_if<Real, 4, 2>(p, s);
+    case 35: return launch_jk_if<Real, 4, 3>(p, s);
+    case 36: return launch_jk_if<Real, 4, 4>(p, s);
+    case 40: return launch_jk_if<Real, 5, 0>(p, s);
+    case 41: return launch_jk_if<Real, 5, 1>(p, s);
+    case 42: return launch_jk_if<Real, 5, 2>(p, s);
+    case 43: return launch_jk_if<Real, 5, 3>(p, s);
+    case 44: return launch_jk_if<Real, 5, 4>(p, s);
+    case 45: return launch_jk_if<Real, 5, 5>(p, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int run_list(fsim_basis* b, int X, int Y, const std::vector<int2>& items, double* d_out, int precision,
+             cudaStream_t s) {
+  if (precision != FSIM_FP64) {
+    set_error("explicit quartet lists are evaluated in FP64 only");
+    return FSIM_EINVAL;
+  }
+  if (items.empty()) return FSIM_OK;
+  int2* d_items = nullptr;
+  FSIM_TRY(dev_alloc(&d_items, items.size()));
+  cudaError_t e = cudaMemcpy(d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    CoopParams<double> p{};
+    p.bra = b->cls[X].view<double>();
+    p.ket = b->cls[Y].view<double>();
+    make_cls_desc(X, p.bd);
+    make_cls_desc(Y, p.kd);
+    p.list_mode = 1;
+    p.items = d_items;
+    p.nitems = (int)items.size();
+    p.out = d_out;
+    p.boys = b->d_boys64;
+    e = launch_coop<double>(p, (p.nitems + kCoopWarps - 1) / kCoopWarps, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  dev_free(d_items);
+  if (e != cudaSuccess) {
+    set_error("ERI list kernel (%d,%d): %s", X, Y, cudaGetErrorString(e));
+    return FSIM_ECUDA;
+  }
+  return FSIM_OK;
+}
+
+// Screened plan for (tau, shard); cached on the basis.
+int get_plan(fsim_basis* b, double tau, int shard, int nshards, int precision, FockPlan** out) {
+  for (FockPlan* p : b->plans)
+    if (p->tau == tau && p->shard == shard && p->nshards == nshards && p->precision == precision) {
+      *out = p;
+      return FSIM_OK;
+    }
+  FockPlan* P = new FockPlan();
+  P->tau = tau;
+  P->shard = shard;
+  P->nshards = nshards;
+  P->precision = precision;
+  b->plans.push_back(P);
+  for (int X = 0; X < kNumPairCls; ++X)
+    for (int Y = 0; Y <= X; ++Y) {
+      ClassPairPlan& cp = P->cp[X][Y];
+      const DevClass& CX = b->cls[X];
+      const DevClass& CY = b->cls[Y];
+      cp.nbra = CX.n;
+      cp.psplit = 1;
+      const int L = pair_cls_la(X) + pair_cls_lb(X) + pair_cls_la(Y) + pair_cls_lb(Y);
+      cp.coop = (precision == FSIM_FP64 && L >= kCoopMinL64) ? 1 : 0;
+      cp.tq = cp.coop ? kCoopWarps : kJKThreads / cp.psplit;
+      if (CX.n == 0 || CY.n == 0) continue;
+      const int tq = cp.tq;
+      std::vector<int> prefix(CX.n + 1, 0), count(CX.n, 0);
+      for (int i = 0; i < CX.n; ++i) {
+        int cnt;
+        if (tau > 0.0) {
+          // kets sorted by Q descending: count of j with Q_i Q_j >= tau
+          const double qi = CX.h_Q[i];
+          int lo = 0, hi = CY.n;
+          while (lo < hi) {
+            const int mid = (lo + hi) / 2;
+            if (qi * CY.h_Q[mid] >= tau) lo = mid + 1; else hi = mid;
+          }
+          cnt = lo;
+        } else {
+          cnt = CY.n;
+        }
+        if (X == Y) cnt = std::min(cnt, i + 1);
+        if (nshards > 1 && (i % nshards) != shard) cnt = 0;
+        count[i] = cnt;
+        prefix[i + 1] = prefix[i] + (cnt + tq - 1) / tq;
+        cp.nquartets += cnt;
+      }
+      cp.nitems = prefix[CX.n];
+      P->nquartets += cp.nquartets;
+      FSIM_TRY(dev_alloc(&cp.d_prefix, CX.n + 1));
+      FSIM_TRY(dev_alloc(&cp.d_count, CX.n));
+      FSIM_CK(cudaMemcpy(cp.d_prefix, prefix.data(), sizeof(int) * (CX.n + 1), cudaMemcpyHostToDevice));
+      FSIM_CK(cudaMemcpy(cp.d_count, count.data(), sizeof(int) * CX.n, cudaMemcpyHostToDevice));
+    }
+  *out = P;
+  return FSIM_OK;
+}
+
+__global__ void to_float_kernel(const double* __restrict__ in, float* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+// J = (Jacc + Jacc^T)/4, K = (Kacc + Kacc^T)/8 (degeneracy-weighted unique-quartet digestion)
+__global__ void symmetrize_kernel(const double* __restrict__ Ja, const double* __restrict__ Ka, double* __restrict__ J,
+                                  double* __restrict__ K, int N) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+  if (c >= N) return;
+  J[(size_t)r * N + c] = 0.25 * (Ja[(size_t)r * N + c] + Ja[(size_t)c * N + r]);
+  K[(size_t)r * N + c] = 0.125 * (Ka[(size_t)r * N + c] + Ka[(size_t)c * N + r]);
+}
+
+static int ensure_scratch(fsim_basis* b) {
+  const size_t n2 = (size_t)b->nbf * b->nbf;
+  if (!b->d_Jacc) FSIM_TRY(dev_alloc(&b->d_Jacc, n2));
+  if (!b->d_Kacc) FSIM_TRY(dev_alloc(&b->d_Kacc, n2));
+  if (!b->d_D32) FSIM_TRY(dev_alloc(&b->d_D32, n2));
+  return FSIM_OK;
+}
+
+template <typename Real>
+static int launch_all(fsim_basis* b, FockPlan* plan, const Real* Dr, cudaStream_t s) {
+  const Real* boys = std::is_same<Real, double>::value ? (const Real*)b->d_boys64 : (const Real*)b->d_boys32;
+  for (int X = kNumPairCls - 1; X >= 0; --X)
+    for (int Y = X; Y >= 0; --Y) {
+      const ClassPairPlan& cp = plan->cp[X][Y];
+      if (cp.nitems == 0) continue;
+      cudaError_t e;
+      if (cp.coop) {
+        CoopParams<Real> p{};
+        p.bra = b->cls[X].view<Real>();
+        p.ket = b->cls[Y].view<Real>();
+        make_cls_desc(X, p.bd);
+        make_cls_desc(Y, p.kd);
+        p.same = X == Y ? 1 : 0;
+        p.list_mode = 0;
+        p.tile_prefix = cp.d_prefix;
+        p.ket_count = cp.d_count;
+        p.tq = cp.tq;
+        p.nitems = cp.nitems;
+        p.N = b->nbf;
+        p.D = Dr;
+        p.J = b->d_Jacc;
+        p.K = b->d_Kacc;
+        p.boys = boys;
+        e = launch_coop<Real>(p, cp.nitems, s);
+      } else {
+        JKParams<Real> p{b->cls[X].view<Real>(), b->cls[Y].view<Real>(), cp.d_prefix, cp.d_count, cp.nitems,
+                         X == Y ? 1 : 0, cp.psplit, b->nbf, Dr, b->d_Jacc, b->d_Kacc, boys};
+        e = dispatch_jk<Real>(X, Y, p, s);
+      }
+      if (e != cudaSuccess) {
+        set_error("J/K kernel (%d|%d): %s", X, Y, cudaGetErrorString(e));
+        return FSIM_ECUDA;
+      }
+    }
+  return FSIM_OK;
+}
+
+int fock_build_device(fsim_basis* b, const double* dD, double* dJ, double* dK, const fsim_fock_opts& o) {
+  if (o.precision != FSIM_FP64 && o.precision != FSIM_MIXED) {
+    set_error("fsim_fock_build: precision must be FSIM_FP64 or FSIM_MIXED");
+    return FSIM_EINVAL;
+  }
+  if (o.nshards < 1 || o.shard < 0 || o.shard >= o.nshards || !(o.schwarz_tau >= 0.0)) {
+    set_error("fsim_fock_build: bad shard (%d of %d) or tau", o.shard, o.nshards);
+    return FSIM_EINVAL;
+  }
+  if (o.precision == FSIM_MIXED && o.boys_fp64_T != 30.0) {
+    set_error("fsim_fock_build: boys_fp64_T is fixed at 30 in this build");
+    return FSIM_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)o.stream;
+  FSIM_TRY(ensure_schwarz(b));
+  FSIM_TRY(ensure_scratch(b));
+  FockPlan* plan = nullptr;
+  FSIM_TRY(get_plan(b, o.schwarz_tau, o.shard, o.nshards, o.precision, &plan));
+  const int N = b->nbf;
+  const size_t n2 = (size_t)N * N;
+  FSIM_CK(cudaMemsetAsync(b->d_Jacc, 0, n2 * sizeof(double), s));
+  FSIM_CK(cudaMemsetAsync(b->d_Kacc, 0, n2 * sizeof(double), s));
+  if (o.precision == FSIM_MIXED) {
+    to_float_kernel<<<256, 256, 0, s>>>(dD, b->d_D32, n2);
+    FSIM_CK(cudaGetLastError());
+    FSIM_TRY(launch_all<float>(b, plan, b->d_D32, s));
+  } else {
+    FSIM_TRY(launch_all<double>(b, plan, dD, s));
+  }
+  dim3 grid((N + 127) / 128, N);
+  symmetrize_kernel<<<grid, 128, 0, s>>>(b->d_Jacc, b->d_Kacc, dJ, dK, N);
+  FSIM_CK(cudaGetLastError());
+  b->last_quartets = plan->nquartets;
+  return FSIM_OK;
+}
+
+// Map a shell pair to (class, index in class, swapped) after Schwarz sorting.
+struct PairLoc {
+  int cls, idx, swapped;
+};
+
+static std::vector<PairLoc> pair_locations(const fsim_basis* b) {
+  const int ns = b->nshell;
+  std::vector<PairLoc> loc((size_t)ns * ns, PairLoc{-1, -1, 0});
+  for (int X = 0; X < kNumPairCls; ++X)
+    for (int j = 0; j < b->cls[X].n; ++j) {
+      const int A = b->cls[X].h_idx[j].z, B = b->cls[X].h_idx[j].w;
+      loc[(size_t)A * ns + B] = PairLoc{X, j, 0};
+      loc[(size_t)B * ns + A] = PairLoc{X, j, 1};
+    }
+  return loc;
+}
+
+}  // namespace fsim
+
+using namespace fsim;
+
+extern "C" {
+
+void fsim_fock_opts_default(fsim_fock_opts* o) {
+  if (!o) return;
+  o->schwarz_tau = 1e-10;
+  o->precision = FSIM_FP64;
+  o->boys_fp64_T = 30.0;
+  o->ptr_mode = FSIM_PTR_HOST;
+  o->stream = nullptr;
+  o->shard = 0;
+  o->nshards = 1;
+}
+
+int fsim_fock_build(fsim_basis* b, const double* D, double* J, double* K, const fsim_fock_opts* opts) {
+  if (!b || !D || !J || !K) {
+    set_error("fsim_fock_build: null pointer");
+    return FSIM_EINVAL;
+  }
+  fsim_fock_opts o;
+  fsim_fock_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.ptr_mode == FSIM_PTR_DEVICE) return fock_build_device(b, D, J, K, o);
+  if (o.ptr_mode != FSIM_PTR_HOST) {
+    set_error("fsim_fock_build: bad ptr_mode");
+    return FSIM_EINVAL;
+  }
+  const size_t n2 = (size_t)b->nbf * b->nbf;
+  cudaStream_t s = (cudaStream_t)o.stream;
+  if (!b->d_D) FSIM_TRY(dev_alloc(&b->d_D, n2));
+  if (!b->d_J) FSIM_TRY(dev_alloc(&b->d_J, n2));
+  if (!b->d_K) FSIM_TRY(dev_alloc(&b->d_K, n2));
+  FSIM_CK(cudaMemcpyAsync(b->d_D, D, n2 * sizeof(double), cudaMemcpyHostToDevice, s));
+  FSIM_TRY(fock_build_device(b, b->d_D, b->d_J, b->d_K, o));
+  FSIM_CK(cudaMemcpyAsync(J, b->d_J, n2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  FSIM_CK(cudaMemcpyAsync(K, b->d_K, n2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  FSIM_CK(cudaStreamSynchronize(s));
+  return FSIM_OK;
+}
+
+long long fsim_last_quartet_count(const fsim_basis* b) { return b ? b->last_quartets : -1; }
+
+int fsim_eri_quartets(fsim_basis* b, int n, const int* quartets, double* out, int precision) {
+  if (!b || (n > 0 && (!quartets || !out)) || n < 0) {
+    set_error("fsim_eri_quartets: bad arguments");
+    return FSIM_EINVAL;
+  }
+  if (precision != FSIM_FP64) {
+    set_error("fsim_eri_quartets: only FSIM_FP64 blocks are exposed");
+    return FSIM_EINVAL;
+  }
+  FSIM_TRY(ensure_schwarz(b));
+  const int ns = b->nshell;
+  const std::vector<PairLoc> loc = pair_locations(b);
+  struct Req {
+    int q;         // request index
+    int i, j;      // bra / ket pair indices in their classes
+    int sw_bk;     // bra and ket swapped
+    int sw1, sw2;  // stored pair order swapped (bra, ket as stored)
+  };
+  std::vector<Req> groups[kNumPairCls][kNumPairCls];
+  std::vector<size_t> out_off(n + 1, 0);
+  for (int q = 0; q < n; ++q) {
+    const int* s4 = quartets + 4 * q;
+    for (int k = 0; k < 4; ++k)
+      if (s4[k] < 0 || s4[k] >= ns) {
+        set_error("fsim_eri_quartets: shell index out of range in quartet %d", q);
+        return FSIM_EINVAL;
+      }
+    size_t sz = 1;
+    for (int k = 0; k < 4; ++k) sz *= ncart(b->sh_l[s4[k]]);
+    out_off[q + 1] = out_off[q] + sz;
+    PairLoc p1 = loc[(size_t)s4[0] * ns + s4[1]], p2 = loc[(size_t)s4[2] * ns + s4[3]];
+    int sw = 0;
+    if (p1.cls < p2.cls) {
+      std::swap(p1, p2);
+      sw = 1;
+    }
+    groups[p1.cls][p2.cls].push_back(Req{q, p1.idx, p2.idx, sw, p1.swapped, p2.swapped});
+  }
+  for (int X = 0; X < kNumPairCls; ++X)
+    for (int Y = 0; Y <= X; ++Y) {
+      auto& G = groups[X][Y];
+      if (G.empty()) continue;
+      const int ncb = ncart(pair_cls_la(X)) * ncart(pair_cls_lb(X));
+      const int nck = ncart(pair_cls_la(Y)) * ncart(pair_cls_lb(Y));
+      std::vector<int2> items(G.size());
+      for (size_t t = 0; t < G.size(); ++t) items[t] = make_int2(G[t].i, G[t].j);
+      double* d_out = nullptr;
+      FSIM_TRY(dev_alloc(&d_out, G.size() * ncb * nck));
+      int rc = run_list(b, X, Y, items, d_out, FSIM_FP64, 0);
+      std::vector<double> h(G.size() * ncb * nck);
+      if (rc == FSIM_OK && cudaMemcpy(h.data(), d_out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = FSIM_ECUDA;
+      dev_free(d_out);
+      if (rc != FSIM_OK) return rc;
+      const int nbA = ncart(pair_cls_lb(X)), nkB = ncart(pair_cls_lb(Y));
+      const int naA = ncart(pair_cls_la(X)), nkA = ncart(pair_cls_la(Y));
+      for (size_t t = 0; t < G.size(); ++t) {
+        const Req& r = G[t];
+        const int* s4 = quartets + 4 * r.q;
+        const int n0 = ncart(b->sh_l[s4[0]]), n1 = ncart(b->sh_l[s4[1]]), n2c = ncart(b->sh_l[s4[2]]),
+                  n3 = ncart(b->sh_l[s4[3]]);
+        double* o = out + out_off[r.q];
+        const double* blk = h.data() + t * ncb * nck;
+        for (int x0 = 0; x0 < n0; ++x0)
+          for (int x1 = 0; x1 < n1; ++x1)
+            for (int x2 = 0; x2 < n2c; ++x2)
+              for (int x3 = 0; x3 < n3; ++x3) {
+                // user (ab|cd) -> stored bra pair (first,second) and ket pair
+                int ub0 = x0, ub1 = x1, uk0 = x2, uk1 = x3;
+                if (r.sw_bk) {
+                  std::swap(ub0, uk0);
+                  std::swap(ub1, uk1);
+                }
+                const int sb0 = r.sw1 ? ub1 : ub0, sb1 = r.sw1 ? ub0 : ub1;
+                const int sk0 = r.sw2 ? uk1 : uk0, sk1 = r.sw2 ? uk0 : uk1;
+                (void)naA; (void)nkA;
+                o[((x0 * n1 + x1) * n2c + x2) * n3 + x3] = blk[(sb0 * nbA + sb1) * nck + sk0 * nkB + sk1];
+              }
+      }
+    }
+  return FSIM_OK;
+}
+
+int fsim_eri_dump(fsim_basis* b, double* g, int precision) {
+  if (!b || !g) {
+    set_error("fsim_eri_dump: null pointer");
+    return FSIM_EINVAL;
+  }
+  if (b->nbf > 64) {
+    set_error("fsim_eri_dump: nbf %d > 64", b->nbf);
+    return FSIM_EINVAL;
+  }
+  const int ns = b->nshell, N = b->nbf;
+  std::vector<int> qs;
+  for (int a = 0; a < ns; ++a)
+    for (int bb = 0; bb <= a; ++bb)
+      for (int c = 0; c <= a; ++c)
+        for (int d = 0; d <= (c == a ? bb : c); ++d) {
+          qs.push_back(a); qs.push_back(bb); qs.push_back(c); qs.push_back(d);
+        }
+  const int nq = (int)qs.size() / 4;
+  size_t tot = 0;
+  std::vector<size_t> off(nq);
+  for (int q = 0; q < nq; ++q) {
+    off[q] = tot;
+    size_t sz = 1;
+    for (int k = 0; k < 4; ++k) sz *= ncart(b->sh_l[qs[4 * q + k]]);
+    tot += sz;
+  }
+  std::vector<double> blocks(tot);
+  FSIM_TRY(fsim_eri_quartets(b, nq, qs.data(), blocks.data(), precision));
+  for (int q = 0; q < nq; ++q) {
+    const int s[4] = {qs[4 * q], qs[4 * q + 1], qs[4 * q + 2], qs[4 * q + 3]};
+    int nc[4];
+    for (int k = 0; k < 4; ++k) nc[k] = ncart(b->sh_l[s[k]]);
+    const double* blk = blocks.data() + off[q];
+    for (int x0 = 0; x0 < nc[0]; ++x0)
+      for (int x1 = 0; x1 < nc[1]; ++x1)
+        for (int x2 = 0; x2 < nc[2]; ++x2)
+          for (int x3 = 0; x3 < nc[3]; ++x3) {
+            const double v = blk[((x0 * nc[1] + x1) * nc[2] + x2) * nc[3] + x3];
+            const size_t m = b->sh_ao[s[0]] + x0, nn = b->sh_ao[s[1]] + x1, l = b->sh_ao[s[2]] + x2,
+                         sg = b->sh_ao[s[3]] + x3;
+            const size_t idx[8][4] = {{m, nn, l, sg}, {nn, m, l, sg}, {m, nn, sg, l}, {nn, m, sg, l},
+                                      {l, sg, m, nn}, {sg, l, m, nn}, {l, sg, nn, m}, {sg, l, nn, m}};
+            for (auto& t : idx) g[((t[0] * N + t[1]) * N + t[2]) * N + t[3]] = v;
+          }
+  }
+  return FSIM_OK;
+}
+
+}  // extern "C"
