@@ -1,0 +1,355 @@
+#!/usr/bin/env python3
+"""Benchmark of the McMurchie-Davidson RHF hot path on GB300.
+
+A step is one Fock build J, K <- D (fsim_fock_build: Boys, Hermite Coulomb
+recursion, Hermite-to-Cartesian contraction and J/K digestion of every unique
+shell quartet that survives Schwarz screening) of the seeded (H2O)_8 cluster
+(152 Cartesian functions, tau = 1e-10) in mixed precision (FP32 integrals,
+FP64 J/K accumulation).  Basis, pair data, Schwarz bounds and quartet lists
+are built once before timing.  value = ERI quartets/s; the FP64 Fock build,
+Fock builds/s and the time to an RHF energy within 1e-8 Eh (mixed vs FP64)
+are reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one rank per GPU) the bra pairs are sharded over the
+ranks (fsim_fock_opts.shard) and J, K are summed with one NCCL all-reduce per
+build: the same total work on N GPUs (strong scaling).  --impl reference times
+the CPU oracle (tests-only code) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ERI quartets/s, Fock builds/s, time-to-RHF-energy at 1e-8 Eh: mixed vs FP64"
+UNIT = "ERI quartets/s"
+WORKLOAD = "water8"
+WORKLOAD_DESC = "(H2O)_8 seeded cluster, 152 Cartesian s/p/d functions, Schwarz tau 1e-10"
+NPRIM = 3  # primitives per shell in every synthetic basis
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
+FP64_PEAK_TFLOPS = 1.25                             # GB300 FP64 (non-tensor), nominal
+
+
+def ncart(l):
+    return (l + 1) * (l + 2) // 2
+
+
+def nherm(L):
+    return (L + 1) * (L + 2) * (L + 3) // 6
+
+
+PAIR_L = [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (2, 2)]
+
+
+def flops_per_quartet(X, Y, nprim=NPRIM):
+    """Algorithmic flops of one contracted quartet of class pair (X|Y):
+    per primitive quartet 2 sum_n n_h(L-n) (R recursion) +
+    2 min(A H1 H2 + A C H2, C H1 H2 + A C H1) (Hermite contraction), plus
+    12 A C per contracted quartet (J/K digestion, 6 FMA per integral)."""
+    (la, lb), (lc, ld) = PAIR_L[X], PAIR_L[Y]
+    L = la + lb + lc + ld
+    A, Cc = ncart(la) * ncart(lb), ncart(lc) * ncart(ld)
+    H1, H2 = nherm(la + lb), nherm(lc + ld)
+    rec = 2 * sum(nherm(L - n) for n in range(L + 1))
+    con = 2 * min(A * H1 * H2 + A * Cc * H2, Cc * H1 * H2 + A * Cc * H1)
+    return nprim ** 4 * (rec + con) + 12 * A * Cc
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.lines, self.proc = [], None
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def cpu_sample(mol, seconds_target: float, tau: float):
+    """The oracle's J/K over a bounded sample of bra pairs: (quartets/s, desc, cores)."""
+    import numpy as np
+    from oracle import OracleBasis
+    ob = OracleBasis(mol)
+    D = np.random.default_rng(0).standard_normal((ob.nbf, ob.nbf)) * 0.05
+    D = D + D.T
+    Q = ob.schwarz()  # noqa: F841  (warms the oracle's Schwarz path like a first build)
+    stride = 64
+    t0 = time.perf_counter()
+    _, _, nq = ob.jk_sample(D, tau, stride)
+    dt = time.perf_counter() - t0
+    # scale the sample toward the target duration (bounded below by every 4th bra pair)
+    stride2 = max(4, int(stride * dt / max(seconds_target, 1e-3)))
+    if stride2 < stride:
+        t0 = time.perf_counter()
+        _, _, nq = ob.jk_sample(D, tau, stride2)
+        dt = time.perf_counter() - t0
+        stride = stride2
+    return nq / dt, nq, dt, stride
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from fsim_synth import workload
+    mol = workload(WORKLOAD)
+    vals, desc = [], ""
+    per_step = 8.0
+    for it in range(args.warmup + args.steps):
+        v, nq, dt, stride = cpu_sample(mol, per_step, args.tau)
+        if it >= args.warmup:
+            vals.append(v)
+        desc = f"bra pairs ij with ij % {stride} == 0 ({nq} unique quartets, {dt:.1f} s per step)"
+    v = statistics.mean(vals)
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "precision": "FP64 oracle (plain C, OpenMP)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_to_energy(res, e_ref, tol=1e-8):
+    """Seconds until the energy stays within tol of e_ref for the rest of the run."""
+    E, T = res["energies"], res["times"]
+    ok = [abs(e - e_ref) < tol for e in E]
+    for i in range(len(E)):
+        if all(ok[i:]):
+            return float(T[i])
+    return None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from fsim_synth import workload
+    from paper_2510_24968_gb300 import FSIM_FP64, FSIM_MIXED, Basis
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    mol = workload(WORKLOAD)
+
+    # CPU baseline first (rank 0, N = 1): the oracle as it stands on the host cores
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, nq, dt, stride = cpu_sample(mol, 15.0, args.tau)
+        cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"oracle J/K of (H2O)_8 over bra pairs ij % {stride} == 0: {nq} unique quartets in {dt:.1f} s"}
+
+    gb = Basis(mol)
+    gb.schwarz()
+    N = gb.nbf
+    Dn = np.random.default_rng(0).standard_normal((N, N)) * 0.05
+    Dn = Dn + Dn.T
+    D = torch.from_numpy(Dn).to(dev)
+    J, K = torch.zeros_like(D), torch.zeros_like(D)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def build(prec, timing=False):
+        gb.fock_build(D, J, K, tau=args.tau, precision=prec, stream=sptr, shard=rank, nshards=world,
+                      timing=timing)
+        if world > 1:
+            torch.distributed.all_reduce(J)
+            torch.distributed.all_reduce(K)
+
+    def timed(prec, steps, warmup):
+        for _ in range(warmup):
+            build(prec)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        per_class, launches, quartets = {}, 0, 0
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            build(prec, timing=True)
+            ev[k][1].record(stream)
+            t, q, n = gb.last_class_times()
+            launches += n
+            quartets = sum(q.values())
+            for key, ms in t.items():
+                per_class.setdefault(key, []).append(ms)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+        if world > 1:
+            tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            ms = float(tt.item())
+            qq = torch.tensor([quartets], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(qq)
+            quartets = int(qq.item())
+        return ms / steps, quartets, per_class, launches, q
+
+    clocks = ClockSampler(local)
+    ms_mixed, q_mixed, cls_mixed, launches, qcls = timed(FSIM_MIXED, args.steps, args.warmup)
+    clk = clocks.stop()
+    ms_fp64, q_fp64, cls_fp64, _, _ = timed(FSIM_FP64, max(2, min(args.steps, 3)), 1)
+
+    # roofline of the dominant kernel (largest time share of the mixed build)
+    tot = {k: sum(v) for k, v in cls_mixed.items()}
+    dom = max(tot, key=tot.get)
+    avg_ms = tot[dom] / len(cls_mixed[dom])
+    fl = qcls[dom] * flops_per_quartet(*dom)
+    achieved = fl / (avg_ms * 1e-3) / 1e12
+    names = ["ss", "ps", "pp", "ds", "dp", "dd"]
+    all_fl = sum(qcls[k] * flops_per_quartet(*k) for k in qcls)
+
+    # end to end through the C-ABI with pinned host buffers (copies inside the timed region)
+    Dh = torch.empty((N, N), dtype=torch.float64, pin_memory=True)
+    Dh.copy_(torch.from_numpy(Dn))
+    Jh = torch.empty((N, N), dtype=torch.float64, pin_memory=True)
+    Kh = torch.empty((N, N), dtype=torch.float64, pin_memory=True)
+    Dnp, Jnp, Knp = Dh.numpy(), Jh.numpy(), Kh.numpy()
+    for _ in range(2):
+        gb.fock_build(Dnp, Jnp, Knp, tau=args.tau, precision=FSIM_MIXED, stream=sptr, shard=rank, nshards=world)
+    t0 = time.perf_counter()
+    ne = max(3, args.steps)
+    for _ in range(ne):
+        gb.fock_build(Dnp, Jnp, Knp, tau=args.tau, precision=FSIM_MIXED, stream=sptr, shard=rank, nshards=world)
+    e2e_s = (time.perf_counter() - t0) / ne
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+
+    # time to a converged energy, mixed vs FP64 (rank 0, whole molecule on one GPU)
+    tte = None
+    if rank == 0 and not args.no_scf:
+        r64 = gb.scf(precision=FSIM_FP64, tau=args.tau, stream=sptr)
+        rmx = gb.scf(precision=FSIM_MIXED, tau=args.tau, stream=sptr)
+        tte = {"fp64_s": time_to_energy(r64, r64["e_total"]), "mixed_s": time_to_energy(rmx, r64["e_total"]),
+               "fp64_iters": r64["iters"], "mixed_iters": rmx["iters"], "mixed_fp64_builds": rmx["fp64_builds"],
+               "mixed_vs_fp64_eh": rmx["e_total"] - r64["e_total"], "e_total_fp64": r64["e_total"]}
+        gold = os.path.join(ROOT, "tests", "golden", "water8_scf_oracle.json")
+        if os.path.exists(gold):
+            with open(gold) as f:
+                g = json.load(f)
+            tte["fp64_vs_oracle_eh"] = r64["e_total"] - g["e_total"]
+            tte["mixed_vs_oracle_eh"] = rmx["e_total"] - g["e_total"]
+        if tte["fp64_s"] and tte["mixed_s"]:
+            tte["speedup"] = tte["fp64_s"] / tte["mixed_s"]
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    value = q_mixed / (ms_mixed * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "nbf": N, "unique_quartets_per_build": q_mixed,
+                   "precision": "mixed: FP32 Boys/R/contraction, FP64 J/K accumulation",
+                   "step": "one Fock build J,K <- D", "l2": "256 MiB write before every timed step",
+                   "parallelism": f"bra-pair shards x{world}" if world > 1 else "1 GPU"},
+        "fock_builds_per_s": {"mixed": 1e3 / ms_mixed, "fp64": 1e3 / ms_fp64},
+        "eri_quartets_per_s": {"mixed": value, "fp64": q_fp64 / (ms_fp64 * 1e-3)},
+        "time_to_energy_1e-8": tte,
+        "roofline": {"kernel": f"jk_kernel<float> ({names[dom[0]]}|{names[dom[1]]})", "bound": "alu",
+                     "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                     "share_of_build": tot[dom] / sum(tot.values())},
+        "build_roofline": {"achieved": all_fl / (ms_mixed * 1e-3) / 1e12, "unit": "TFLOP/s",
+                           "frac_fp32": all_fl / (ms_mixed * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                           "fp64_achieved": all_fl / (ms_fp64 * 1e-3) / 1e12,
+                           "frac_fp64": all_fl / (ms_fp64 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS},
+        "class_ms": {f"{names[k[0]]}|{names[k[1]]}": round(tot[k] / len(cls_mixed[k]), 4) for k in tot},
+        "cpu_baseline": cpu,
+        "e2e": {"value": q_mixed / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * N * 8,
+                "d2h_bytes_per_step": 2 * N * N * 8},
+        "clocks": clk,
+        "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--tau", type=float, default=1e-10)
+    ap.add_argument("--no-scf", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -38,7 +38,7 @@ extern "C" {
 #define FSIM_ENOMEM (-6)          /* device allocation failed */
 
 #define FSIM_FP64 0   /* every step in FP64 */
-#define FSIM_MIXED 1  /* FP32 Hermite integrals + contraction, FP64 J/K accumulation, FP64 Boys above boys_fp64_T */
+#define FSIM_MIXED 1  /* FP32 Boys, Hermite integrals and contraction; FP64 J/K accumulation */
 
 #define FSIM_PTR_HOST 0
 #define FSIM_PTR_DEVICE 1
@@ -104,14 +104,15 @@ int fsim_schwarz(fsim_basis* b, double* Q);
 typedef struct {
   double schwarz_tau;  /* skip unique quartets with Q_ab Q_cd < tau; 0 = no screening */
   int precision;       /* FSIM_FP64 or FSIM_MIXED */
-  double boys_fp64_T;  /* mixed path: Boys in FP64 for T above this (fixed at 30; other values are rejected) */
+  double boys_fp64_T;  /* mixed path: Boys in FP64 for T >= this; 0 = never; values in (0, 30) are rejected */
   int ptr_mode;        /* FSIM_PTR_HOST or FSIM_PTR_DEVICE for D, J, K */
   void* stream;        /* cudaStream_t; NULL = legacy default stream */
   int shard;           /* this shard's index in [0, nshards): bra pairs i with i % nshards == shard */
   int nshards;         /* 1 = whole build */
+  int timing;          /* 1: record CUDA events around each class-pair kernel (fsim_last_class_times) */
 } fsim_fock_opts;
 
-/* Fills the defaults: tau 1e-10, FP64, boys_fp64_T 30, host pointers, NULL stream, 1 shard. */
+/* Fills the defaults: tau 1e-10, FP64, boys_fp64_T 0, host pointers, NULL stream, 1 shard. */
 void fsim_fock_opts_default(fsim_fock_opts* o);
 
 /*
@@ -131,10 +132,21 @@ int fsim_fock_build(fsim_basis* b, const double* D, double* J, double* K, const 
 long long fsim_last_quartet_count(const fsim_basis* b);
 
 /*
- * Contracted ERI blocks (mu nu|la si) for explicit shell quartets, by the same
- * kernels as the Fock build (debug / parity).  quartets: 4*n shell indices
- * (a,b,c,d); out: concatenated blocks, each na*nb*nc*nd in (a,b,c,d)
- * row-major order; host pointers; precision FSIM_FP64 or FSIM_MIXED.
+ * Per class pair (bra pair class X >= ket pair class Y, index X*6+Y; classes
+ * ss ps pp ds dp dd) of the last fsim_fock_build: kernel time in ms from CUDA
+ * events recorded on the build's stream (only when opts.timing was set; else
+ * -1), and unique quartets evaluated.  ms, quartets: 36 entries each (host).
+ * *nlaunch: kernels the build launched.  Synchronises the build's stream.
+ */
+int fsim_last_class_times(fsim_basis* b, float* ms, long long* quartets, int* nlaunch);
+
+/*
+ * Contracted ERI blocks (mu nu|la si) for explicit shell quartets (debug /
+ * parity), by the FP64 warp-cooperative quartet kernel that also serves the
+ * Schwarz diagonal and the FP64 Fock build of the classes with la+lb+lc+ld >= 5.
+ * quartets: 4*n shell indices (a,b,c,d); out: concatenated blocks, each
+ * na*nb*nc*nd in (a,b,c,d) row-major order; host pointers; precision must be
+ * FSIM_FP64.
  */
 int fsim_eri_quartets(fsim_basis* b, int n, const int* quartets, double* out, int precision);
 

@@ -55,6 +55,8 @@ def lib():
             L.orc_schwarz.argtypes = [C.c_void_p, _dp]
             L.orc_jk.argtypes = [C.c_void_p, _dp, _dp, _dp, C.c_double, C.c_int,
                                  C.POINTER(C.c_longlong)]
+            L.orc_jk_sample.argtypes = [C.c_void_p, _dp, _dp, _dp, C.c_double, C.c_int,
+                                        C.POINTER(C.c_longlong), C.c_int]
             L.orc_jk_block.argtypes = [C.c_void_p, _dp, C.c_int, C.c_int, _dp, _dp, C.c_double, _dp]
             L.orc_jacobi_eigh.restype = C.c_int
             L.orc_jacobi_eigh.argtypes = [C.c_int, _dp, _dp, _dp]
@@ -153,6 +155,16 @@ class OracleBasis:
         Q = np.ascontiguousarray(Q, dtype=np.float64).reshape(-1)
         lib().orc_jk_block(self.h, D, int(sa), int(sb), Jb, Kb, float(tau), Q)
         return Jb.reshape(na, nb), Kb.reshape(na, nb)
+
+    def jk_sample(self, D: np.ndarray, tau: float, bra_stride: int, nthreads: int = 0):
+        """J/K contributions of the bra pairs ij with ij % bra_stride == 0 (timing sample)."""
+        N = self.nbf
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        J = np.zeros((N, N))
+        K = np.zeros((N, N))
+        nq = C.c_longlong(0)
+        lib().orc_jk_sample(self.h, D, J, K, float(tau), int(nthreads), C.byref(nq), int(bra_stride))
+        return J, K, nq.value
 
     def jk(self, D: np.ndarray, tau: float = 0.0, nthreads: int = 0):
         """(J, K, n_unique_quartets_evaluated) over unique shell quartets."""

@@ -69,7 +69,7 @@ template <int LA, int LB>
 __global__ void pair_data_kernel(int n, int ppmax, const int4* __restrict__ idx, const double* __restrict__ cen,
                                  const double* __restrict__ alpha, const double* __restrict__ coef,
                                  const int* __restrict__ nprim, double* __restrict__ pd64,
-                                 float* __restrict__ pd32) {
+                                 float* __restrict__ pd32, double4* __restrict__ pq64, float4* __restrict__ pq32) {
   using PC = PairCls<LA, LB>;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * ppmax) return;
@@ -83,6 +83,8 @@ __global__ void pair_data_kernel(int n, int ppmax, const int4* __restrict__ idx,
     pd32[f * fs + (size_t)k * n + j] = (float)v;
   };
   if (k >= Ka * Kb) {
+    pq64[(size_t)k * n + j] = make_double4(1.0, 0.0, 0.0, 0.0);
+    pq32[(size_t)k * n + j] = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
     put(0, 1.0);
     put(1, 0.0); put(2, 0.0); put(3, 0.0);
     for (int z = 0; z < PC::NNZ; ++z) put(4 + z, 0.0);
@@ -122,9 +124,11 @@ __global__ void pair_data_kernel(int n, int ppmax, const int4* __restrict__ idx,
   }
   // sqrt(2) pi^{5/4} / p folds half of 2 pi^{5/2} / (p q) into each pair
   const double scale = coef[sa * kMaxPrim + ka] * coef[sb * kMaxPrim + kb] * 1.41421356237309504880 *
-                       4.17455651896716104160 /* pi^{5/4} */ / p;
+                       4.18251339837959907596 /* pi^{5/4} */ / p;
   put(0, p);
   put(1, P[0]); put(2, P[1]); put(3, P[2]);
+  pq64[(size_t)k * n + j] = make_double4(p, P[0], P[1], P[2]);
+  pq32[(size_t)k * n + j] = make_float4((float)p, (float)P[0], (float)P[1], (float)P[2]);
   static_for<PC::NC>([&](auto Aa) {
     constexpr int ac = decltype(Aa)::value;
     constexpr int ia = ac / PC::NB, ib = ac % PC::NB;
@@ -140,16 +144,16 @@ __global__ void pair_data_kernel(int n, int ppmax, const int4* __restrict__ idx,
 }
 
 static cudaError_t launch_pair_data(int cls, int n, int ppmax, const int4* idx, const fsim_basis* b, double* pd64,
-                                    float* pd32) {
+                                    float* pd32, double4* pq64, float4* pq32) {
   const int total = n * ppmax, th = 128, bl = (total + th - 1) / th;
   if (total == 0) return cudaSuccess;
   switch (cls) {
-    case 0: pair_data_kernel<0, 0><<<bl, th>>>(n, ppmax, idx, b->d_cen, b->d_alpha, b->d_coef, b->d_nprim, pd64, pd32); break;
-    case 1: pair_data_kernel<1, 0><<<bl, th>>>(n, ppmax, idx, b->d_cen, b->d_alpha, b->d_coef, b->d_nprim, pd64, pd32); break;
-    case 2: pair_data_kernel<1, 1><<<bl, th>>>(n, ppmax, idx, b->d_cen, b->d_alpha, b->d_coef, b->d_nprim, pd64, pd32); break;
-    case 3: pair_data_kernel<2, 0><<<bl, th>>>(n, ppmax, idx, b->d_cen, b->d_alpha, b->d_coef, b->d_nprim, pd64, pd32); break;
-    case 4: pair_data_kernel<2, 1><<<bl, th>>>(n, ppmax, idx, b->d_cen, b->d_alpha, b->d_coef, b->d_nprim, pd64, pd32); break;
-    default: pair_data_kernel<2, 2><<<bl, th>>>(n, ppmax, idx, b->d_cen, b->d_alpha, b->d_coef, b->d_nprim, pd64, pd32); break;
+    case 0: pair_data_kernel<0, 0><<<bl, th>>>(n, ppmax, idx, b->d_cen, b->d_alpha, b->d_coef, b->d_nprim, pd64, pd32, pq64, pq32); break;
+    case 1: pair_data_kernel<1, 0><<<bl, th>>>(n, ppmax, idx, b->d_cen, b->d_alpha, b->d_coef, b->d_nprim, pd64, pd32, pq64, pq32); break;
+    case 2: pair_data_kernel<1, 1><<<bl, th>>>(n, ppmax, idx, b->d_cen, b->d_alpha, b->d_coef, b->d_nprim, pd64, pd32, pq64, pq32); break;
+    case 3: pair_data_kernel<2, 0><<<bl, th>>>(n, ppmax, idx, b->d_cen, b->d_alpha, b->d_coef, b->d_nprim, pd64, pd32, pq64, pq32); break;
+    case 4: pair_data_kernel<2, 1><<<bl, th>>>(n, ppmax, idx, b->d_cen, b->d_alpha, b->d_coef, b->d_nprim, pd64, pd32, pq64, pq32); break;
+    default: pair_data_kernel<2, 2><<<bl, th>>>(n, ppmax, idx, b->d_cen, b->d_alpha, b->d_coef, b->d_nprim, pd64, pd32, pq64, pq32); break;
   }
   return cudaGetLastError();
 }
@@ -157,7 +161,7 @@ static cudaError_t launch_pair_data(int cls, int n, int ppmax, const int4* idx, 
 // (Re)build the device data of pair class `cls` in the given pair order.
 int build_pair_data(fsim_basis* b, int cls, const std::vector<int4>& order) {
   DevClass& C = b->cls[cls];
-  dev_free(C.idx); dev_free(C.npp); dev_free(C.pd64); dev_free(C.pd32);
+  dev_free(C.idx); dev_free(C.npp); dev_free(C.pd64); dev_free(C.pd32); dev_free(C.pq64); dev_free(C.pq32);
   C.n = (int)order.size();
   C.nnz = pair_cls_nnz(cls);
   C.h_idx = order;
@@ -172,9 +176,11 @@ int build_pair_data(fsim_basis* b, int cls, const std::vector<int4>& order) {
   FSIM_TRY(dev_alloc(&C.npp, C.n));
   FSIM_TRY(dev_alloc(&C.pd64, (size_t)C.nfield() * C.ppmax * C.n));
   FSIM_TRY(dev_alloc(&C.pd32, (size_t)C.nfield() * C.ppmax * C.n));
+  FSIM_TRY(dev_alloc(&C.pq64, (size_t)C.ppmax * C.n));
+  FSIM_TRY(dev_alloc(&C.pq32, (size_t)C.ppmax * C.n));
   FSIM_CK(cudaMemcpy(C.idx, order.data(), sizeof(int4) * C.n, cudaMemcpyHostToDevice));
   FSIM_CK(cudaMemcpy(C.npp, C.h_npp.data(), sizeof(int) * C.n, cudaMemcpyHostToDevice));
-  FSIM_CK(launch_pair_data(cls, C.n, C.ppmax, C.idx, b, C.pd64, C.pd32));
+  FSIM_CK(launch_pair_data(cls, C.n, C.ppmax, C.idx, b, C.pd64, C.pd32, C.pq64, C.pq32));
   return FSIM_OK;
 }
 
@@ -242,7 +248,7 @@ __global__ void onee_kernel(int which, int nshell, const int* __restrict__ lsh, 
         for (int nuc = 0; nuc < natom; ++nuc) {
           const double X = P[0] - axyz[3 * nuc], Y = P[1] - axyz[3 * nuc + 1], Z = P[2] - axyz[3 * nuc + 2];
           double F[5];
-          boys_fp64<4>(p * (X * X + Y * Y + Z * Z), F, boys);
+          boys_fp64<4>(p * (X * X + Y * Y + Z * Z), F, boys + 4, kBoysCols);
           // R^n_{tuv} for n + t + u + v <= L: level arrays, highest n first
           double R[5][35];
           for (int n = L; n >= 0; --n) {
@@ -450,7 +456,7 @@ int fsim_basis_create(const fsim_atom* atoms, int natom, const fsim_shell_desc* 
 void fsim_basis_destroy(fsim_basis* b) {
   if (!b) return;
   for (auto& C : b->cls) {
-    dev_free(C.idx); dev_free(C.npp); dev_free(C.pd64); dev_free(C.pd32);
+    dev_free(C.idx); dev_free(C.npp); dev_free(C.pd64); dev_free(C.pd32); dev_free(C.pq64); dev_free(C.pq32);
   }
   for (auto* p : b->plans) {
     for (auto& row : p->cp)
@@ -465,6 +471,9 @@ void fsim_basis_destroy(fsim_basis* b) {
   dev_free(b->d_boys64); dev_free(b->d_boys32);
   dev_free(b->d_Jacc); dev_free(b->d_Kacc); dev_free(b->d_D); dev_free(b->d_J); dev_free(b->d_K);
   dev_free(b->d_D32);
+  if (b->ev_ok)
+    for (auto& pr : b->ev)
+      for (auto& e : pr) cudaEventDestroy(e);
   delete b;
 }
 

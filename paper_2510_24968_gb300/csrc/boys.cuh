@@ -10,9 +10,11 @@
 //     precision there) and the upward recursion F_{n+1} = ((2n+1)F_n - e^{-T})/(2T),
 //     which is stable for large T.
 // FP64: h = 1/16, K = 8, table to T = 36 (truncation < 1e-16 relative).
-// FP32: h = 1/8, K = 5, table to T = 30; above T = 30 the value is evaluated in
-// FP64 by the asymptotic branch and rounded (the mixed-precision policy keeps
-// Boys in FP64 at large T).
+// FP32: h = 1/8, K = 5, table to T = 30; above T = 30 the asymptotic branch
+// runs in FP32 (F_0 = sqrt(pi/T)/2, e^{-T} kept in the upward recursion), or
+// in FP64 above a caller-chosen threshold `t64` (the policy of keeping Boys in
+// FP64 at large T; on GB300 FP64 issues at a small fraction of the FP32 rate,
+// so that policy is an option, not the default).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -47,15 +49,18 @@ __device__ __forceinline__ void boys_asymptotic(double T, double (&F)[L + 1]) {
   }
 }
 
+// `tabL` points at column L of grid row 0; consecutive grid rows are `stride`
+// apart (the full table in global memory, or only the columns L..L+K-1
+// staged in shared memory).
 template <int L>
-__device__ __forceinline__ void boys_fp64(double T, double (&F)[L + 1], const double* __restrict__ tab) {
+__device__ __forceinline__ void boys_fp64(double T, double (&F)[L + 1], const double* __restrict__ tabL, int stride) {
   if (T < kBoysTmax64) {
     int i = __double2int_rn(T * (1.0 / kBoysH64));
     double x = i * kBoysH64 - T;  // -(T - T_i)
-    const double* row = tab + i * kBoysCols + L;
-    double acc = __ldg(row + kBoysK64 - 1);
+    const double* row = tabL + i * stride;
+    double acc = row[kBoysK64 - 1];
 #pragma unroll
-    for (int k = kBoysK64 - 1; k >= 1; --k) acc = fma(acc, x * inv_int(k), __ldg(row + k - 1));
+    for (int k = kBoysK64 - 1; k >= 1; --k) acc = fma(acc, x * inv_int(k), row[k - 1]);
     F[L] = acc;
     if (L > 0) {
       double e = exp(-T);
@@ -69,20 +74,30 @@ __device__ __forceinline__ void boys_fp64(double T, double (&F)[L + 1], const do
 }
 
 template <int L>
-__device__ __forceinline__ void boys_fp32(float T, float (&F)[L + 1], const float* __restrict__ tab) {
+__device__ __forceinline__ void boys_fp32(float T, float (&F)[L + 1], const float* __restrict__ tabL, int stride,
+                                          float t64) {
   if (T < kBoysTmax32) {
     int i = __float2int_rn(T * (1.0f / kBoysH32));
     float x = i * kBoysH32 - T;
-    const float* row = tab + i * kBoysCols + L;
-    float acc = __ldg(row + kBoysK32 - 1);
+    const float* row = tabL + i * stride;
+    float acc = row[kBoysK32 - 1];
 #pragma unroll
-    for (int k = kBoysK32 - 1; k >= 1; --k) acc = fmaf(acc, x * (float)inv_int(k), __ldg(row + k - 1));
+    for (int k = kBoysK32 - 1; k >= 1; --k) acc = fmaf(acc, x * (float)inv_int(k), row[k - 1]);
     F[L] = acc;
     if (L > 0) {
       float e = expf(-T);
       float T2 = 2.0f * T;
 #pragma unroll
       for (int n = L - 1; n >= 0; --n) F[n] = fmaf(T2, F[n + 1], e) * (float)inv_odd(n);
+    }
+  } else if (T < t64) {
+    const float rs = rsqrtf(T);
+    F[0] = 0.5f * (float)kSqrtPi * rs;
+    if (L > 0) {
+      const float e = expf(-T);
+      const float h = 0.5f * rs * rs;
+#pragma unroll
+      for (int n = 1; n <= L; ++n) F[n] = ((2 * n - 1) * F[n - 1] - e) * h;
     }
   } else {
     double Fd[L + 1];
@@ -96,16 +111,20 @@ template <typename Real>
 struct Boys;
 template <>
 struct Boys<double> {
+  static constexpr int K = kBoysK64, NROW = kBoysN64;
   template <int L>
-  static __device__ __forceinline__ void eval(double T, double (&F)[L + 1], const double* tab) {
-    boys_fp64<L>(T, F, tab);
+  static __device__ __forceinline__ void eval(double T, double (&F)[L + 1], const double* tabL, int stride,
+                                              float /*t64*/) {
+    boys_fp64<L>(T, F, tabL, stride);
   }
 };
 template <>
 struct Boys<float> {
+  static constexpr int K = kBoysK32, NROW = kBoysN32;
   template <int L>
-  static __device__ __forceinline__ void eval(float T, float (&F)[L + 1], const float* tab) {
-    boys_fp32<L>(T, F, tab);
+  static __device__ __forceinline__ void eval(float T, float (&F)[L + 1], const float* tabL, int stride,
+                                              float t64) {
+    boys_fp32<L>(T, F, tabL, stride, t64);
   }
 };
 

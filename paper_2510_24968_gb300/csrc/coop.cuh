@@ -71,29 +71,30 @@ struct CoopParams {
   double* J;
   double* K;
   const Real* __restrict__ boys;
+  float boys64_T;  // FP32 path: Boys in FP64 at T >= this (infinity = never)
 };
 
 // Boys F_0..F_L for a runtime L <= 8 in the working precision.
 template <typename Real, int L>
-__device__ __forceinline__ void boys_to(Real T, Real* F, const Real* tab) {
+__device__ __forceinline__ void boys_to(Real T, Real* F, const Real* tab, float t64) {
   Real f[L + 1];
-  Boys<Real>::template eval<L>(T, f, tab);
+  Boys<Real>::template eval<L>(T, f, tab + L, kBoysCols, t64);
 #pragma unroll
   for (int n = 0; n <= L; ++n) F[n] = f[n];
 }
 
 template <typename Real>
-__device__ __forceinline__ void boys_rt(int L, Real T, Real* F, const Real* tab) {
+__device__ __forceinline__ void boys_rt(int L, Real T, Real* F, const Real* tab, float t64) {
   switch (L) {
-    case 0: boys_to<Real, 0>(T, F, tab); break;
-    case 1: boys_to<Real, 1>(T, F, tab); break;
-    case 2: boys_to<Real, 2>(T, F, tab); break;
-    case 3: boys_to<Real, 3>(T, F, tab); break;
-    case 4: boys_to<Real, 4>(T, F, tab); break;
-    case 5: boys_to<Real, 5>(T, F, tab); break;
-    case 6: boys_to<Real, 6>(T, F, tab); break;
-    case 7: boys_to<Real, 7>(T, F, tab); break;
-    default: boys_to<Real, 8>(T, F, tab); break;
+    case 0: boys_to<Real, 0>(T, F, tab, t64); break;
+    case 1: boys_to<Real, 1>(T, F, tab, t64); break;
+    case 2: boys_to<Real, 2>(T, F, tab, t64); break;
+    case 3: boys_to<Real, 3>(T, F, tab, t64); break;
+    case 4: boys_to<Real, 4>(T, F, tab, t64); break;
+    case 5: boys_to<Real, 5>(T, F, tab, t64); break;
+    case 6: boys_to<Real, 6>(T, F, tab, t64); break;
+    case 7: boys_to<Real, 7>(T, F, tab, t64); break;
+    default: boys_to<Real, 8>(T, F, tab, t64); break;
   }
 }
 
@@ -159,18 +160,20 @@ __global__ void __launch_bounds__(kCoopWarps * 32) coop_kernel(CoopParams<Real> 
     for (int m = 0; m < kCoopMaxOut; ++m) outv[m] = Real(0);
     for (int b = 0; b < nppb; ++b) {
       const Real* bp = P.bra.pd + (size_t)b * P.bra.n + i;
-      const Real p = bp[0], Px = bp[bst], Py = bp[2 * bst], Pz = bp[3 * bst];
+      const auto b4 = P.bra.pq[(size_t)b * P.bra.n + i];
+      const Real p = b4.x, Px = b4.y, Py = b4.z, Pz = b4.w;
       Real Wv[kCoopMaxW];
 #pragma unroll
       for (int m = 0; m < kCoopMaxW; ++m) Wv[m] = Real(0);
       for (int k = 0; k < nppk; ++k) {
         const Real* kp = P.ket.pd + (size_t)k * P.ket.n + j;
-        const Real q = kp[0], X = Px - kp[kst], Y = Py - kp[2 * kst], Z = Pz - kp[3 * kst];
+        const auto k4 = P.ket.pq[(size_t)k * P.ket.n + j];
+        const Real q = k4.x, X = Px - k4.y, Y = Py - k4.z, Z = Pz - k4.w;
         const Real s = p + q;
         const Real rs = rsqrt_r<Real>(s);
         const Real al = p * q * (rs * rs);
         Real F[kBoysMaxN + 1];
-        boys_rt<Real>(L, al * (X * X + Y * Y + Z * Z), F, P.boys);
+        boys_rt<Real>(L, al * (X * X + Y * Y + Z * Z), F, P.boys, P.boys64_T);
         // source terms (-2 al)^n F_n / sqrt(p+q)
         Real fac = rs;
         for (int n = 0; n <= L; ++n) {

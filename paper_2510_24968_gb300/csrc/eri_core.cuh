@@ -31,12 +31,24 @@ constexpr int kJKThreads = 128;
 // Primitive-pair data is SoA: value (field f, primitive pair k, pair j) at
 // pd[(f * ppmax + k) * n + j]; fields: 0 = p, 1..3 = P, 4.. = E non-zeros.
 template <typename Real>
+struct Vec4;
+template <>
+struct Vec4<double> {
+  using type = double4;
+};
+template <>
+struct Vec4<float> {
+  using type = float4;
+};
+
+template <typename Real>
 struct PairView {
   int n;
   int ppmax;
-  const int4* __restrict__ idx;  // (ao_a, ao_b, shell_a, shell_b)
-  const int* __restrict__ npp;   // primitive pairs of each pair
-  const Real* __restrict__ pd;
+  const int4* __restrict__ idx;                     // (ao_a, ao_b, shell_a, shell_b)
+  const int* __restrict__ npp;                      // primitive pairs of each pair
+  const Real* __restrict__ pd;                      // [field][pp][pair]
+  const typename Vec4<Real>::type* __restrict__ pq;  // (p, Px, Py, Pz) at [pp][pair]
 };
 
 template <typename Real>
@@ -52,6 +64,7 @@ struct JKParams {
   double* J;                            // accumulators (FP64), N x N
   double* K;
   const Real* __restrict__ boys;
+  float boys64_T;                       // FP32 path: Boys in FP64 at T >= this (infinity = never)
 };
 
 // Hermite Coulomb integrals R^0_{tuv} for t+u+v <= L, in place (Eq. R-recursion):
@@ -118,7 +131,7 @@ struct KetChunks {
 template <typename Real, int LA, int LB, int LC, int LD, int CS, int CH, class BraAt>
 __device__ __forceinline__ void quartet_chunk(Real (&out)[PairCls<LA, LB>::NC][CS], const BraAt& bra, int nppb,
                                               int b0, int bstep, const PairView<Real>& ket, int j, int nppk,
-                                              const Real* __restrict__ boys) {
+                                              const Real* __restrict__ boysL, int bstride, float t64) {
   using BC = PairCls<LA, LB>;
   using KC = PairCls<LC, LD>;
   using KCh = KetChunks<KC, CS>;
@@ -144,8 +157,8 @@ __device__ __forceinline__ void quartet_chunk(Real (&out)[PairCls<LA, LB>::NC][C
 
     for (int k = 0; k < nppk; ++k) {
       const Real* kp = ket.pd + (size_t)k * ket.n + j;
-      const Real q = __ldg(kp), Qx = __ldg(kp + kstride), Qy = __ldg(kp + 2 * kstride),
-                 Qz = __ldg(kp + 3 * kstride);
+      const auto q4 = ket.pq[(size_t)k * ket.n + j];
+      const Real q = q4.x, Qx = q4.y, Qy = q4.z, Qz = q4.w;
       Real Ek[NZ];
 #pragma unroll
       for (int z = 0; z < NZ; ++z) Ek[z] = __ldg(kp + (size_t)(4 + nzoff + z) * kstride);
@@ -155,7 +168,7 @@ __device__ __forceinline__ void quartet_chunk(Real (&out)[PairCls<LA, LB>::NC][C
       const Real X = Px - Qx, Y = Py - Qy, Z = Pz - Qz;
       const Real T = al * (X * X + Y * Y + Z * Z);
       Real F[L + 1];
-      Boys<Real>::template eval<L>(T, F, boys);
+      Boys<Real>::template eval<L>(T, F, boysL, bstride, t64);
       Real src[L + 1];
       Real fac = rs;
       const Real m2a = Real(-2) * al;
@@ -207,149 +220,130 @@ __device__ __forceinline__ int find_bra(const int* __restrict__ prefix, int n, i
   return lo;
 }
 
-// Fused ERI + J/K kernel.  One CTA = one (bra pair, tile of kets); thread =
-// (ket, bra-primitive subset).  Accumulates J_acc, K_acc with the 8-fold
-// degeneracy factor; the caller symmetrises J = (J_acc + J_acc^T)/4 and
-// K = (K_acc + K_acc^T)/8.
+// Fused ERI + J/K kernel, persistent: each CTA walks work items (bra pair,
+// tile of kets) with a grid stride; threads = (ket, bra-primitive subset).
+// Shared memory: the Boys table columns L..L+K-1 (loaded once per CTA), the
+// bra block of D, the bra block of J_acc and the bra primitive data.
+// Accumulates J_acc, K_acc with the 8-fold degeneracy factor; the caller
+// symmetrises J = (J_acc + J_acc^T)/4 and K = (K_acc + K_acc^T)/8.
+template <typename Real>
+__host__ __device__ constexpr size_t jk_boys_smem() {
+  return (size_t)Boys<Real>::NROW * Boys<Real>::K * sizeof(Real);
+}
+
 template <typename Real, int LA, int LB, int LC, int LD, int CS>
 __global__ void __launch_bounds__(kJKThreads) jk_kernel(JKParams<Real> P) {
   using BC = PairCls<LA, LB>;
   using KC = PairCls<LC, LD>;
+  constexpr int L = LA + LB + LC + LD;
   constexpr int NFB = 4 + BC::NNZ;
+  constexpr int BK = Boys<Real>::K, BR = Boys<Real>::NROW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* sDab = reinterpret_cast<double*>(smem_raw);   // D_{mu nu} of the bra block
-  double* sJab = sDab + BC::NC;                         // J_acc partial of the bra block
-  Real* sbra = reinterpret_cast<Real*>(sJab + BC::NC);  // bra primitive data [pp][field]
+  constexpr int NWARP = kJKThreads / 32;
+  Real* sBoys = reinterpret_cast<Real*>(smem_raw);                     // [BR][BK]
+  Real* sDab = reinterpret_cast<Real*>(smem_raw + (jk_boys_smem<Real>() + 15) / 16 * 16);  // D bra block
+  Real* sJw = sDab + BC::NC;               // per-warp partials of J_acc for the bra block [warp][a]
+  Real* sbra = sJw + NWARP * BC::NC;       // bra primitive data [pp][field]
 
-  const int item = blockIdx.x;
-  if (item >= P.nitems) return;
-  const int i = find_bra(P.tile_prefix, P.bra.n, item);
-  const int tile = item - __ldg(P.tile_prefix + i);
-  const int4 bi = P.bra.idx[i];
-  const int nppb = P.bra.npp[i];
+  for (int x = threadIdx.x; x < BR * BK; x += blockDim.x)
+    sBoys[x] = P.boys[(x / BK) * kBoysCols + L + x % BK];
   const int N = P.N;
-
-  for (int x = threadIdx.x; x < nppb * NFB; x += blockDim.x) {
-    const int pp = x / NFB, f = x % NFB;
-    sbra[x] = P.bra.pd[((size_t)f * P.bra.ppmax + pp) * P.bra.n + i];
-  }
-  for (int x = threadIdx.x; x < BC::NC; x += blockDim.x) {
-    sDab[x] = (double)P.D[(size_t)(bi.x + x / BC::NB) * N + bi.y + x % BC::NB];
-    sJab[x] = 0.0;
-  }
-  __syncthreads();
-
   const int ps = P.psplit;
   const int tq = blockDim.x / ps;
   const int q = threadIdx.x / ps, bs = threadIdx.x % ps;
-  const int j = tile * tq + q;
-  Real jb[BC::NC];  // this thread's part of J_acc for the bra block
+  const int lane = threadIdx.x & 31;
+
+  for (int item = blockIdx.x; item < P.nitems; item += gridDim.x) {
+    const int i = find_bra(P.tile_prefix, P.bra.n, item);
+    const int tile = item - __ldg(P.tile_prefix + i);
+    const int4 bi = P.bra.idx[i];
+    const int nppb = P.bra.npp[i];
+    __syncthreads();  // previous item done with the bra buffers
+    for (int x = threadIdx.x; x < nppb * NFB; x += blockDim.x) {
+      const int pp = x / NFB, f = x % NFB;
+      sbra[x] = P.bra.pd[((size_t)f * P.bra.ppmax + pp) * P.bra.n + i];
+    }
+    for (int x = threadIdx.x; x < BC::NC; x += blockDim.x) sDab[x] = P.D[(size_t)(bi.x + x / BC::NB) * N + bi.y + x % BC::NB];
+    __syncthreads();
+
+    const int j = tile * tq + q;
+    Real jb[BC::NC];  // this thread's part of J_acc for the bra block
 #pragma unroll
-  for (int a = 0; a < BC::NC; ++a) jb[a] = Real(0);
-  if (q < tq && j < __ldg(P.ket_count + i)) {
-    const int4 ki = P.ket.idx[j];
-    const int nppk = P.ket.npp[j];
-    const Real deg = Real((bi.z == bi.w ? 1 : 2) * (ki.z == ki.w ? 1 : 2) * ((P.same && i == j) ? 1 : 2));
-    auto bra = [&](int f, int pp) -> Real { return sbra[pp * NFB + f]; };
-    static_for<KetChunks<KC, CS>::NCH>([&](auto Ch) {
-      constexpr int ch = decltype(Ch)::value;
-      Real out[BC::NC][CS];
-      quartet_chunk<Real, LA, LB, LC, LD, CS, ch>(out, bra, nppb, bs, ps, P.ket, j, nppk, P.boys);
-      // digestion (Eq. fock) of this chunk
+    for (int a = 0; a < BC::NC; ++a) jb[a] = Real(0);
+    if (q < tq && j < __ldg(P.ket_count + i)) {
+      const int4 ki = P.ket.idx[j];
+      const int nppk = P.ket.npp[j];
+      const Real deg = Real((bi.z == bi.w ? 1 : 2) * (ki.z == ki.w ? 1 : 2) * ((P.same && i == j) ? 1 : 2));
+      auto bra = [&](int f, int pp) -> Real { return sbra[pp * NFB + f]; };
+      static_for<KetChunks<KC, CS>::NCH>([&](auto Ch) {
+        constexpr int ch = decltype(Ch)::value;
+        Real out[BC::NC][CS];
+        quartet_chunk<Real, LA, LB, LC, LD, CS, ch>(out, bra, nppb, bs, ps, P.ket, j, nppk, sBoys, BK, P.boys64_T);
+        // digestion (Eq. fock) of this chunk
 #pragma unroll
-      for (int cs = 0; cs < CS; ++cs) {
-        const int c = ch * CS + cs;
-        const int lam = ki.x + c / KC::NB, sig = ki.y + c % KC::NB;
-        // J_ket[la si] += sum_a D_ab v ; J_bra[a] += D_{la si} v
-        const Real Dls = P.D[(size_t)lam * N + sig];
-        Real jk = Real(0);
+        for (int cs = 0; cs < CS; ++cs) {
+          const int c = ch * CS + cs;
+          const int lam = ki.x + c / KC::NB, sig = ki.y + c % KC::NB;
+          // J_ket[la si] += sum_a D_ab v ; J_bra[a] += D_{la si} v
+          const Real Dls = P.D[(size_t)lam * N + sig];
+          Real jk = Real(0);
 #pragma unroll
-        for (int a = 0; a < BC::NC; ++a) {
-          const Real v = deg * out[a][cs];
-          jk = fma((Real)sDab[a], v, jk);
-          jb[a] = fma(Dls, v, jb[a]);
-        }
-        atomicAdd(&P.J[(size_t)lam * N + sig], (double)jk);
-        // K: (mu la) += D_nu si v ; (nu si) += D_mu la v ; (mu si) += D_nu la v ; (nu la) += D_mu si v
-#pragma unroll
-        for (int ia = 0; ia < BC::NA; ++ia) {
-          const int mu = bi.x + ia;
-          Real k1 = Real(0), k3 = Real(0);
-#pragma unroll
-          for (int ib = 0; ib < BC::NB; ++ib) {
-            const int nu = bi.y + ib;
-            const Real v = deg * out[ia * BC::NB + ib][cs];
-            k1 = fma(P.D[(size_t)nu * N + sig], v, k1);
-            k3 = fma(P.D[(size_t)nu * N + lam], v, k3);
+          for (int a = 0; a < BC::NC; ++a) {
+            const Real v = deg * out[a][cs];
+            jk = fma(sDab[a], v, jk);
+            jb[a] = fma(Dls, v, jb[a]);
           }
-          atomicAdd(&P.K[(size_t)mu * N + lam], (double)k1);
-          atomicAdd(&P.K[(size_t)mu * N + sig], (double)k3);
-        }
-#pragma unroll
-        for (int ib = 0; ib < BC::NB; ++ib) {
-          const int nu = bi.y + ib;
-          Real k2 = Real(0), k4 = Real(0);
+          atomicAdd(&P.J[(size_t)lam * N + sig], (double)jk);
+          // K: (mu la) += D_nu si v ; (nu si) += D_mu la v ; (mu si) += D_nu la v ; (nu la) += D_mu si v
 #pragma unroll
           for (int ia = 0; ia < BC::NA; ++ia) {
             const int mu = bi.x + ia;
-            const Real v = deg * out[ia * BC::NB + ib][cs];
-            k2 = fma(P.D[(size_t)mu * N + lam], v, k2);
-            k4 = fma(P.D[(size_t)mu * N + sig], v, k4);
+            Real k1 = Real(0), k3 = Real(0);
+#pragma unroll
+            for (int ib = 0; ib < BC::NB; ++ib) {
+              const int nu = bi.y + ib;
+              const Real v = deg * out[ia * BC::NB + ib][cs];
+              k1 = fma(P.D[(size_t)nu * N + sig], v, k1);
+              k3 = fma(P.D[(size_t)nu * N + lam], v, k3);
+            }
+            atomicAdd(&P.K[(size_t)mu * N + lam], (double)k1);
+            atomicAdd(&P.K[(size_t)mu * N + sig], (double)k3);
           }
-          atomicAdd(&P.K[(size_t)nu * N + sig], (double)k2);
-          atomicAdd(&P.K[(size_t)nu * N + lam], (double)k4);
+#pragma unroll
+          for (int ib = 0; ib < BC::NB; ++ib) {
+            const int nu = bi.y + ib;
+            Real k2 = Real(0), k4 = Real(0);
+#pragma unroll
+            for (int ia = 0; ia < BC::NA; ++ia) {
+              const int mu = bi.x + ia;
+              const Real v = deg * out[ia * BC::NB + ib][cs];
+              k2 = fma(P.D[(size_t)mu * N + lam], v, k2);
+              k4 = fma(P.D[(size_t)mu * N + sig], v, k4);
+            }
+            atomicAdd(&P.K[(size_t)nu * N + sig], (double)k2);
+            atomicAdd(&P.K[(size_t)nu * N + lam], (double)k4);
+          }
         }
-      }
-    });
+      });
+    }
+    // J_bra: warp reduction (every lane takes part, idle lanes hold zeros), one
+    // shared-memory partial per warp and element, one FP64 global add per CTA
+    // and element
+    const int warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int a = 0; a < BC::NC; ++a) {
+      Real v = jb[a];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) sJw[warp * BC::NC + a] = v;
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < BC::NC; x += blockDim.x) {
+      double v = 0.0;
+      for (int w = 0; w < NWARP; ++w) v += (double)sJw[w * BC::NC + x];
+      atomicAdd(&P.J[(size_t)(bi.x + x / BC::NB) * N + bi.y + x % BC::NB], v);
+    }
   }
-  // J_bra: warp reduction (every lane takes part, idle lanes hold zeros), one
-  // shared-memory add per warp and element, one global add per CTA and element
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int a = 0; a < BC::NC; ++a) {
-    Real v = jb[a];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) atomicAdd(&sJab[a], (double)v);
-  }
-  __syncthreads();
-  for (int x = threadIdx.x; x < BC::NC; x += blockDim.x)
-    atomicAdd(&P.J[(size_t)(bi.x + x / BC::NB) * N + bi.y + x % BC::NB], sJab[x]);
-}
-
-// Explicit list of (bra, ket) pair indices; writes each contracted block
-// out[item * NCb * NCk + a * NCk + c] in FP64.  Used for the Schwarz
-// diagonal, the debug ERI dump and sampled parity checks.
-template <typename Real>
-struct ListParams {
-  PairView<Real> bra, ket;
-  const int2* __restrict__ items;
-  int nitems;
-  double* out;
-  const Real* __restrict__ boys;
-};
-
-template <typename Real, int LA, int LB, int LC, int LD, int CS>
-__global__ void __launch_bounds__(kJKThreads) list_kernel(ListParams<Real> P) {
-  using BC = PairCls<LA, LB>;
-  using KC = PairCls<LC, LD>;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= P.nitems) return;
-  const int2 it = P.items[t];
-  const int i = it.x, j = it.y;
-  const int nppb = P.bra.npp[i], nppk = P.ket.npp[j];
-  const size_t bstride = (size_t)P.bra.ppmax * P.bra.n;
-  auto bra = [&](int f, int pp) -> Real { return __ldg(P.bra.pd + (size_t)f * bstride + (size_t)pp * P.bra.n + i); };
-  double* o = P.out + (size_t)t * BC::NC * KC::NC;
-  static_for<KetChunks<KC, CS>::NCH>([&](auto Ch) {
-    constexpr int ch = decltype(Ch)::value;
-    Real out[BC::NC][CS];
-    quartet_chunk<Real, LA, LB, LC, LD, CS, ch>(out, bra, nppb, 0, 1, P.ket, j, nppk, P.boys);
-#pragma unroll
-    for (int a = 0; a < BC::NC; ++a)
-#pragma unroll
-      for (int cs = 0; cs < CS; ++cs) o[a * KC::NC + ch * CS + cs] = (double)out[a][cs];
-  });
 }
 
 }  // namespace fsim

@@ -2,6 +2,8 @@
 // Each eri_inst_XY.cu instantiates them for FP64 and FP32 so that the 21
 // class pairs compile in parallel.
 #pragma once
+#include <algorithm>
+
 #include "fsim_internal.h"
 
 namespace fsim {
@@ -25,19 +27,25 @@ __host__ __device__ constexpr int chunk_size(int X, int Y) {
   return 1;
 }
 
+// Persistent launch: grid = min(work items, resident CTAs on the device).
+int device_sm_count();
+
 template <typename Real, int X, int Y>
 cudaError_t launch_jk(const JKParams<Real>& p, cudaStream_t s) {
   constexpr int LA = pair_cls_la(X), LB = pair_cls_lb(X), LC = pair_cls_la(Y), LD = pair_cls_lb(Y);
   constexpr int CS = chunk_size<Real>(X, Y);
   using BC = PairCls<LA, LB>;
   auto k = jk_kernel<Real, LA, LB, LC, LD, CS>;
-  const size_t smem = 2 * BC::NC * sizeof(double) + (size_t)p.bra.ppmax * (4 + BC::NNZ) * sizeof(Real);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  const size_t smem = (jk_boys_smem<Real>() + 15) / 16 * 16 + (1 + kJKThreads / 32) * BC::NC * sizeof(Real) +
+                      (size_t)p.bra.ppmax * (4 + BC::NNZ) * sizeof(Real);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   if (p.nitems == 0) return cudaSuccess;
-  k<<<p.nitems, kJKThreads, smem, s>>>(p);
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kJKThreads, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = std::min(p.nitems, std::max(1, occ) * device_sm_count());
+  k<<<grid, kJKThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
 

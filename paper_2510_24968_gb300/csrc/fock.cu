@@ -20,6 +20,17 @@ extern template cudaError_t launch_coop<float>(const CoopParams<float>&, int, cu
 
 int ensure_schwarz(fsim_basis* b);
 
+int device_sm_count() {
+  static int n = 0;
+  if (n <= 0) {
+    int d = 0;
+    cudaGetDevice(&d);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
 template <typename Real, int X, int Y>
 static cudaError_t launch_jk_if(const JKParams<Real>& p, cudaStream_t s) {
   constexpr int L = pair_cls_la(X) + pair_cls_lb(X) + pair_cls_la(Y) + pair_cls_lb(Y);
@@ -79,6 +90,7 @@ int run_list(fsim_basis* b, int X, int Y, const std::vector<int2>& items, double
     p.nitems = (int)items.size();
     p.out = d_out;
     p.boys = b->d_boys64;
+    p.boys64_T = INFINITY;
     e = launch_coop<double>(p, (p.nitems + kCoopWarps - 1) / kCoopWarps, s);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -112,9 +124,7 @@ int get_plan(fsim_basis* b, double tau, int shard, int nshards, int precision, F
       cp.psplit = 1;
       const int L = pair_cls_la(X) + pair_cls_lb(X) + pair_cls_la(Y) + pair_cls_lb(Y);
       cp.coop = (precision == FSIM_FP64 && L >= kCoopMinL64) ? 1 : 0;
-      cp.tq = cp.coop ? kCoopWarps : kJKThreads / cp.psplit;
       if (CX.n == 0 || CY.n == 0) continue;
-      const int tq = cp.tq;
       std::vector<int> prefix(CX.n + 1, 0), count(CX.n, 0);
       for (int i = 0; i < CX.n; ++i) {
         int cnt;
@@ -133,9 +143,18 @@ int get_plan(fsim_basis* b, double tau, int shard, int nshards, int precision, F
         if (X == Y) cnt = std::min(cnt, i + 1);
         if (nshards > 1 && (i % nshards) != shard) cnt = 0;
         count[i] = cnt;
-        prefix[i + 1] = prefix[i] + (cnt + tq - 1) / tq;
         cp.nquartets += cnt;
       }
+      // class pairs with few quartets split the bra primitive pairs over
+      // several threads so that the launch still covers the device
+      if (!cp.coop) {
+        const long long target = (long long)device_sm_count() * 2 * kJKThreads;
+        for (int ps : {3, 9})
+          if (cp.nquartets * cp.psplit < target && ps <= CX.ppmax) cp.psplit = ps;
+      }
+      cp.tq = cp.coop ? kCoopWarps : kJKThreads / cp.psplit;
+      const int tq = cp.tq;
+      for (int i = 0; i < CX.n; ++i) prefix[i + 1] = prefix[i] + (count[i] + tq - 1) / tq;
       cp.nitems = prefix[CX.n];
       P->nquartets += cp.nquartets;
       FSIM_TRY(dev_alloc(&cp.d_prefix, CX.n + 1));
@@ -170,12 +189,17 @@ static int ensure_scratch(fsim_basis* b) {
 }
 
 template <typename Real>
-static int launch_all(fsim_basis* b, FockPlan* plan, const Real* Dr, cudaStream_t s) {
+static int launch_all(fsim_basis* b, FockPlan* plan, const Real* Dr, float boys64_T, bool timing, cudaStream_t s) {
   const Real* boys = std::is_same<Real, double>::value ? (const Real*)b->d_boys64 : (const Real*)b->d_boys32;
   for (int X = kNumPairCls - 1; X >= 0; --X)
     for (int Y = X; Y >= 0; --Y) {
       const ClassPairPlan& cp = plan->cp[X][Y];
+      const int ci = X * kNumPairCls + Y;
+      b->last_class_q[ci] = cp.nquartets;
+      b->last_class_run[ci] = cp.nitems > 0;
       if (cp.nitems == 0) continue;
+      ++b->last_launches;
+      if (timing) FSIM_CK(cudaEventRecord(b->ev[ci][0], s));
       cudaError_t e;
       if (cp.coop) {
         CoopParams<Real> p{};
@@ -194,16 +218,18 @@ static int launch_all(fsim_basis* b, FockPlan* plan, const Real* Dr, cudaStream_
         p.J = b->d_Jacc;
         p.K = b->d_Kacc;
         p.boys = boys;
+        p.boys64_T = boys64_T;
         e = launch_coop<Real>(p, cp.nitems, s);
       } else {
         JKParams<Real> p{b->cls[X].view<Real>(), b->cls[Y].view<Real>(), cp.d_prefix, cp.d_count, cp.nitems,
-                         X == Y ? 1 : 0, cp.psplit, b->nbf, Dr, b->d_Jacc, b->d_Kacc, boys};
+                         X == Y ? 1 : 0, cp.psplit, b->nbf, Dr, b->d_Jacc, b->d_Kacc, boys, boys64_T};
         e = dispatch_jk<Real>(X, Y, p, s);
       }
       if (e != cudaSuccess) {
         set_error("J/K kernel (%d|%d): %s", X, Y, cudaGetErrorString(e));
         return FSIM_ECUDA;
       }
+      if (timing) FSIM_CK(cudaEventRecord(b->ev[ci][1], s));
     }
   return FSIM_OK;
 }
@@ -217,10 +243,11 @@ int fock_build_device(fsim_basis* b, const double* dD, double* dJ, double* dK, c
     set_error("fsim_fock_build: bad shard (%d of %d) or tau", o.shard, o.nshards);
     return FSIM_EINVAL;
   }
-  if (o.precision == FSIM_MIXED && o.boys_fp64_T != 30.0) {
-    set_error("fsim_fock_build: boys_fp64_T is fixed at 30 in this build");
+  if (!(o.boys_fp64_T == 0.0 || o.boys_fp64_T >= 30.0)) {
+    set_error("fsim_fock_build: boys_fp64_T must be 0 (never) or >= 30 (the FP32 table covers T < 30)");
     return FSIM_EINVAL;
   }
+  const float b64 = o.boys_fp64_T > 0.0 ? (float)o.boys_fp64_T : INFINITY;
   cudaStream_t s = (cudaStream_t)o.stream;
   FSIM_TRY(ensure_schwarz(b));
   FSIM_TRY(ensure_scratch(b));
@@ -228,18 +255,29 @@ int fock_build_device(fsim_basis* b, const double* dD, double* dJ, double* dK, c
   FSIM_TRY(get_plan(b, o.schwarz_tau, o.shard, o.nshards, o.precision, &plan));
   const int N = b->nbf;
   const size_t n2 = (size_t)N * N;
+  if (o.timing && !b->ev_ok) {
+    for (auto& pr : b->ev)
+      for (auto& e : pr) FSIM_CK(cudaEventCreate(&e));
+    b->ev_ok = true;
+  }
+  b->last_timed = o.timing != 0;
+  b->last_stream = s;
+  b->last_launches = 0;
+  for (auto& r : b->last_class_run) r = false;
   FSIM_CK(cudaMemsetAsync(b->d_Jacc, 0, n2 * sizeof(double), s));
   FSIM_CK(cudaMemsetAsync(b->d_Kacc, 0, n2 * sizeof(double), s));
   if (o.precision == FSIM_MIXED) {
     to_float_kernel<<<256, 256, 0, s>>>(dD, b->d_D32, n2);
     FSIM_CK(cudaGetLastError());
-    FSIM_TRY(launch_all<float>(b, plan, b->d_D32, s));
+    ++b->last_launches;
+    FSIM_TRY(launch_all<float>(b, plan, b->d_D32, b64, o.timing != 0, s));
   } else {
-    FSIM_TRY(launch_all<double>(b, plan, dD, s));
+    FSIM_TRY(launch_all<double>(b, plan, dD, b64, o.timing != 0, s));
   }
   dim3 grid((N + 127) / 128, N);
   symmetrize_kernel<<<grid, 128, 0, s>>>(b->d_Jacc, b->d_Kacc, dJ, dK, N);
   FSIM_CK(cudaGetLastError());
+  ++b->last_launches;
   b->last_quartets = plan->nquartets;
   return FSIM_OK;
 }
@@ -271,11 +309,27 @@ void fsim_fock_opts_default(fsim_fock_opts* o) {
   if (!o) return;
   o->schwarz_tau = 1e-10;
   o->precision = FSIM_FP64;
-  o->boys_fp64_T = 30.0;
+  o->boys_fp64_T = 0.0;
   o->ptr_mode = FSIM_PTR_HOST;
   o->stream = nullptr;
   o->shard = 0;
   o->nshards = 1;
+  o->timing = 0;
+}
+
+int fsim_last_class_times(fsim_basis* b, float* ms, long long* quartets, int* nlaunch) {
+  if (!b || !ms || !quartets || !nlaunch) {
+    set_error("fsim_last_class_times: null pointer");
+    return FSIM_EINVAL;
+  }
+  FSIM_CK(cudaStreamSynchronize(b->last_stream));
+  for (int ci = 0; ci < kNumPairCls * kNumPairCls; ++ci) {
+    ms[ci] = -1.0f;
+    quartets[ci] = b->last_class_q[ci];
+    if (b->last_timed && b->last_class_run[ci]) FSIM_CK(cudaEventElapsedTime(&ms[ci], b->ev[ci][0], b->ev[ci][1]));
+  }
+  *nlaunch = b->last_launches;
+  return FSIM_OK;
 }
 
 int fsim_fock_build(fsim_basis* b, const double* D, double* J, double* K, const fsim_fock_opts* opts) {

@@ -59,6 +59,8 @@ struct DevClass {
   int* npp = nullptr;
   double* pd64 = nullptr;   // [4 + nnz][ppmax][n]
   float* pd32 = nullptr;
+  double4* pq64 = nullptr;  // (p, P) at [ppmax][n]
+  float4* pq32 = nullptr;
   std::vector<int4> h_idx;  // host copy, same order
   std::vector<int> h_npp;
   std::vector<double> h_Q;  // Schwarz bound of each pair, same order
@@ -69,11 +71,11 @@ struct DevClass {
 
 template <>
 inline PairView<double> DevClass::view<double>() const {
-  return PairView<double>{n, ppmax, idx, npp, pd64};
+  return PairView<double>{n, ppmax, idx, npp, pd64, pq64};
 }
 template <>
 inline PairView<float> DevClass::view<float>() const {
-  return PairView<float>{n, ppmax, idx, npp, pd32};
+  return PairView<float>{n, ppmax, idx, npp, pd32, pq32};
 }
 
 // Screened work list of one class pair (bra class X >= ket class Y).
@@ -139,6 +141,14 @@ struct fsim_basis {
   double* d_J = nullptr;
   double* d_K = nullptr;
   float* d_D32 = nullptr;
+  // per class-pair timing of the last build
+  cudaEvent_t ev[fsim::kNumPairCls * fsim::kNumPairCls][2] = {};
+  bool ev_ok = false;
+  bool last_timed = false;
+  int last_launches = 0;
+  long long last_class_q[fsim::kNumPairCls * fsim::kNumPairCls] = {};
+  bool last_class_run[fsim::kNumPairCls * fsim::kNumPairCls] = {};
+  cudaStream_t last_stream = nullptr;
 };
 
 namespace fsim {

@@ -235,13 +235,14 @@ int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res) {
   SOL_CK(cusolverDnCreate(&c.sol));
   SOL_CK(cusolverDnSetStream(c.sol, c.s));
   Dev mem;
-  double *S, *H, *T, *X, *D, *Dn, *dD, *J, *K, *G, *F, *Fu, *tmp, *tmp2, *e, *scratch;
+  double *S, *H, *T, *X, *D, *Dn, *dD, *J, *K, *G, *F, *Fu, *tmp, *tmp2, *e, *scratch, *Dr;
   FSIM_TRY(mem.alloc(&S, n2)); FSIM_TRY(mem.alloc(&H, n2)); FSIM_TRY(mem.alloc(&T, n2));
   FSIM_TRY(mem.alloc(&X, n2)); FSIM_TRY(mem.alloc(&D, n2)); FSIM_TRY(mem.alloc(&Dn, n2));
   FSIM_TRY(mem.alloc(&dD, n2)); FSIM_TRY(mem.alloc(&J, n2)); FSIM_TRY(mem.alloc(&K, n2));
   FSIM_TRY(mem.alloc(&G, n2)); FSIM_TRY(mem.alloc(&F, n2)); FSIM_TRY(mem.alloc(&Fu, n2));
   FSIM_TRY(mem.alloc(&tmp, n2)); FSIM_TRY(mem.alloc(&tmp2, n2)); FSIM_TRY(mem.alloc(&e, n2));
   FSIM_TRY(mem.alloc(&scratch, 4));
+  FSIM_TRY(mem.alloc(&Dr, n2));  // density of the last FP64 build (mixed path)
   const int m = o.diis_size;
   double *Fh = nullptr, *Eh = nullptr;
   if (m > 0) {
@@ -304,7 +305,12 @@ int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res) {
   fsim_fock_opts fo = o.fock;
   fo.ptr_mode = FSIM_PTR_DEVICE;
   const bool mixed = o.fock.precision == FSIM_MIXED;
-  int phase = mixed ? 0 : 2;  // 0: mixed settling, 1: (unused), 2: final accuracy
+  // phase 0: mixed settling; phase 2: final accuracy.  With final_fp64 each
+  // FP64 build resets G; the iteration only stops once the density has not
+  // moved (rms 1e-6) since the last reset, so the FP32 part of G is tiny.
+  int phase = mixed ? 0 : 2;
+  int nresets = 0;
+  constexpr int kMaxResets = 6;
   bool have_G = false;
   int nstored = 0, head = 0;
   double E_old = 0.0, E = 0.0;
@@ -329,6 +335,10 @@ int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res) {
       FSIM_TRY(fock_build_device(b, D, J, K, fo));
       add_kernel<<<bl, th, 0, c.s>>>(J, K, -0.5, G, n2);
       have_G = true;
+      if (mixed && want64) {
+        FSIM_CK(cudaMemcpyAsync(Dr, D, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c.s));
+        ++nresets;
+      }
     }
     res->quartets += b->last_quartets;
     if (want64) ++res->fp64_builds; else ++res->mixed_builds;
@@ -385,6 +395,15 @@ int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res) {
       continue;
     }
     if (phase == 2 && dE < o.conv_dE && rmsD < o.conv_dD) {
+      if (mixed && o.final_fp64 && nresets < kMaxResets) {
+        const double moved = std::sqrt(host_dot(c, scratch, Dn, Dr, n2, 1, &rc) / (double)n2);
+        if (rc != FSIM_OK) return rc;
+        if (moved > 1e-6) {  // another FP64 reset at the current density
+          have_G = false;
+          have_old = false;
+          continue;
+        }
+      }
       res->converged = 1;
       // the density used for the reported energy is the one F was built from
       FSIM_CK(cudaMemcpyAsync(D, Dn, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c.s));

@@ -32,7 +32,7 @@ FSIM_GUESS_DENSITY = 1
 # every symbol declared in include/fsim.h
 EXPORTS = ["fsim_basis_create", "fsim_basis_destroy", "fsim_basis_nbf", "fsim_basis_nshell",
            "fsim_basis_pair_counts", "fsim_enuc", "fsim_onee", "fsim_schwarz", "fsim_fock_opts_default",
-           "fsim_fock_build", "fsim_last_quartet_count", "fsim_eri_quartets", "fsim_eri_dump",
+           "fsim_fock_build", "fsim_last_quartet_count", "fsim_last_class_times", "fsim_eri_quartets", "fsim_eri_dump",
            "fsim_scf_opts_default", "fsim_scf", "fsim_last_error"]
 
 
@@ -53,7 +53,8 @@ class fsim_shell_desc(C.Structure):
 
 class fsim_fock_opts(C.Structure):
     _fields_ = [("schwarz_tau", C.c_double), ("precision", C.c_int), ("boys_fp64_T", C.c_double),
-                ("ptr_mode", C.c_int), ("stream", C.c_void_p), ("shard", C.c_int), ("nshards", C.c_int)]
+                ("ptr_mode", C.c_int), ("stream", C.c_void_p), ("shard", C.c_int), ("nshards", C.c_int),
+                ("timing", C.c_int)]
 
 
 class fsim_scf_opts(C.Structure):
@@ -97,6 +98,7 @@ def load():
     L.fsim_fock_build.argtypes = [vp, vp, vp, vp, C.POINTER(fsim_fock_opts)]
     L.fsim_last_quartet_count.argtypes = [vp]
     L.fsim_last_quartet_count.restype = C.c_longlong
+    L.fsim_last_class_times.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_longlong), ip]
     L.fsim_eri_quartets.argtypes = [vp, C.c_int, ip, dp, C.c_int]
     L.fsim_eri_dump.argtypes = [vp, dp, C.c_int]
     L.fsim_scf_opts_default.argtypes = [C.POINTER(fsim_scf_opts)]
@@ -200,7 +202,7 @@ class Basis:
         return Q
 
     def fock_build(self, D, J=None, K=None, tau=1e-10, precision=FSIM_FP64, stream=None,
-                   shard=0, nshards=1):
+                   shard=0, nshards=1, boys_fp64_T=0.0, timing=False):
         """J, K for density D (numpy -> host mode; CUDA torch tensors -> device mode)."""
         if J is None:
             J = np.zeros((self.nbf, self.nbf)) if isinstance(D, np.ndarray) else D.new_zeros(D.shape)
@@ -208,6 +210,7 @@ class Basis:
             K = np.zeros((self.nbf, self.nbf)) if isinstance(D, np.ndarray) else D.new_zeros(D.shape)
         o = fsim_fock_opts_default()
         o.schwarz_tau, o.precision, o.shard, o.nshards = tau, precision, shard, nshards
+        o.boys_fp64_T, o.timing = boys_fp64_T, int(timing)
         pD, mode = _ptr_of(D)
         pJ, _ = _ptr_of(J)
         pK, _ = _ptr_of(K)
@@ -218,6 +221,16 @@ class Basis:
 
     def last_quartet_count(self) -> int:
         return load().fsim_last_quartet_count(self.h)
+
+    def last_class_times(self):
+        """({(X, Y): ms}, {(X, Y): quartets}, kernels launched) of the last build."""
+        ms = (C.c_float * 36)()
+        q = (C.c_longlong * 36)()
+        n = C.c_int()
+        _check(load().fsim_last_class_times(self.h, ms, q, C.byref(n)))
+        times = {(i // 6, i % 6): ms[i] for i in range(36) if ms[i] >= 0}
+        quart = {(i // 6, i % 6): q[i] for i in range(36) if i // 6 >= i % 6}
+        return times, quart, n.value
 
     def eri_quartets(self, quartets) -> list:
         q = np.ascontiguousarray(np.asarray(quartets, dtype=np.int32).reshape(-1, 4))
