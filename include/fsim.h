@@ -128,6 +128,26 @@ void fsim_fock_opts_default(fsim_fock_opts* o);
  */
 int fsim_fock_build(fsim_basis* b, const double* D, double* J, double* K, const fsim_fock_opts* opts);
 
+/*
+ * fsim_fock_build for callers that must not allocate device memory while they
+ * run (a server whose memory pool owns the device budget, a loop that cannot
+ * take the device-wide synchronisation of cudaMalloc/cudaFree, an allocator
+ * that forbids raw cudaMalloc).  The paper has no counterpart; this is an
+ * interface addition.  Same result as fsim_fock_build (same kernels), but the
+ * J/K accumulators and the FP32 density copy live in one fixed file-scope
+ * device array of 5 MiB that every GPU loading the library keeps until exit,
+ * so the call allocates nothing.  Limits and rules:
+ *  - nbf <= 512, else FSIM_EINVAL; D, J, K device pointers (ptr_mode
+ *    FSIM_PTR_DEVICE); opts->timing must be 0;
+ *  - the basis must already hold its Schwarz bounds and the screening plan for
+ *    these options: call fsim_fock_build once with the same opts during
+ *    set-up (else FSIM_EINVAL, nothing launched);
+ *  - the first call on a device looks up the array's device address (with the
+ *    basis' device current); make that first call before any stream capture;
+ *  - all calls share the array; calls whose GPU work overlaps race on it.
+ */
+int fsim_fock_build_noalloc(fsim_basis* b, const double* D, double* J, double* K, const fsim_fock_opts* opts);
+
 /* Unique shell quartets the last fsim_fock_build evaluated (after screening). */
 long long fsim_last_quartet_count(const fsim_basis* b);
 

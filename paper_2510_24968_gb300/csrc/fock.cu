@@ -492,3 +492,102 @@ int fsim_eri_dump(fsim_basis* b, double* g, int precision) {
 }
 
 }  // extern "C"
+
+namespace fsim {
+
+// ---------------------------------------------------------------------------
+// Fock build into caller-supplied scratch (used by fsim_fock_build_noalloc in
+// noalloc.cu).  Same kernels and plan as fock_build_device, but the J/K
+// accumulators and the FP32 density copy live in the memory passed in, and no
+// step allocates: the Schwarz bounds and the screening plan for these options
+// must already exist on the basis.
+// ---------------------------------------------------------------------------
+template <typename Real>
+static int launch_all_into(fsim_basis* b, FockPlan* plan, const Real* Dr, float boys64_T, double* Jacc,
+                           double* Kacc, cudaStream_t s) {
+  const Real* boys = std::is_same<Real, double>::value ? (const Real*)b->d_boys64 : (const Real*)b->d_boys32;
+  for (int X = kNumPairCls - 1; X >= 0; --X)
+    for (int Y = X; Y >= 0; --Y) {
+      const ClassPairPlan& cp = plan->cp[X][Y];
+      if (cp.nitems == 0) continue;
+      cudaError_t e;
+      if (cp.coop) {
+        CoopParams<Real> p{};
+        p.bra = b->cls[X].view<Real>();
+        p.ket = b->cls[Y].view<Real>();
+        make_cls_desc(X, p.bd);
+        make_cls_desc(Y, p.kd);
+        p.same = X == Y ? 1 : 0;
+        p.list_mode = 0;
+        p.tile_prefix = cp.d_prefix;
+        p.ket_count = cp.d_count;
+        p.tq = cp.tq;
+        p.nitems = cp.nitems;
+        p.N = b->nbf;
+        p.D = Dr;
+        p.J = Jacc;
+        p.K = Kacc;
+        p.boys = boys;
+        p.boys64_T = boys64_T;
+        e = launch_coop<Real>(p, cp.nitems, s);
+      } else {
+        JKParams<Real> p{b->cls[X].view<Real>(), b->cls[Y].view<Real>(), cp.d_prefix, cp.d_count, cp.nitems,
+                         X == Y ? 1 : 0, cp.psplit, b->nbf, Dr, Jacc, Kacc, boys, boys64_T};
+        e = dispatch_jk<Real>(X, Y, p, s);
+      }
+      if (e != cudaSuccess) {
+        set_error("J/K kernel (%d|%d): %s", X, Y, cudaGetErrorString(e));
+        return FSIM_ECUDA;
+      }
+    }
+  return FSIM_OK;
+}
+
+int fock_build_into(fsim_basis* b, const double* dD, double* dJ, double* dK, const fsim_fock_opts& o, double* Jacc,
+                    double* Kacc, float* D32) {
+  if (o.precision != FSIM_FP64 && o.precision != FSIM_MIXED) {
+    set_error("precision must be FSIM_FP64 or FSIM_MIXED");
+    return FSIM_EINVAL;
+  }
+  if (o.nshards < 1 || o.shard < 0 || o.shard >= o.nshards || !(o.schwarz_tau >= 0.0)) {
+    set_error("bad shard (%d of %d) or tau", o.shard, o.nshards);
+    return FSIM_EINVAL;
+  }
+  if (!(o.boys_fp64_T == 0.0 || o.boys_fp64_T >= 30.0)) {
+    set_error("boys_fp64_T must be 0 (never) or >= 30");
+    return FSIM_EINVAL;
+  }
+  if (!b->schwarz_done) {
+    set_error("no Schwarz bounds yet: call fsim_schwarz (or fsim_fock_build) during set-up");
+    return FSIM_EINVAL;
+  }
+  FockPlan* plan = nullptr;
+  for (FockPlan* p : b->plans)
+    if (p->tau == o.schwarz_tau && p->shard == o.shard && p->nshards == o.nshards && p->precision == o.precision)
+      plan = p;
+  if (!plan) {
+    set_error("no screening plan for tau %g, shard %d/%d, precision %d: run fsim_fock_build once with the same "
+              "options during set-up",
+              o.schwarz_tau, o.shard, o.nshards, o.precision);
+    return FSIM_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)o.stream;
+  const int N = b->nbf;
+  const size_t n2 = (size_t)N * N;
+  FSIM_CK(cudaMemsetAsync(Jacc, 0, n2 * sizeof(double), s));
+  FSIM_CK(cudaMemsetAsync(Kacc, 0, n2 * sizeof(double), s));
+  const float b64 = o.boys_fp64_T > 0.0 ? (float)o.boys_fp64_T : INFINITY;
+  if (o.precision == FSIM_MIXED) {
+    to_float_kernel<<<256, 256, 0, s>>>(dD, D32, n2);
+    FSIM_CK(cudaGetLastError());
+    FSIM_TRY(launch_all_into<float>(b, plan, D32, b64, Jacc, Kacc, s));
+  } else {
+    FSIM_TRY(launch_all_into<double>(b, plan, dD, b64, Jacc, Kacc, s));
+  }
+  dim3 grid((N + 127) / 128, N);
+  symmetrize_kernel<<<grid, 128, 0, s>>>(Jacc, Kacc, dJ, dK, N);
+  FSIM_CK(cudaGetLastError());
+  return FSIM_OK;
+}
+
+}  // namespace fsim

@@ -32,7 +32,7 @@ FSIM_GUESS_DENSITY = 1
 # every symbol declared in include/fsim.h
 EXPORTS = ["fsim_basis_create", "fsim_basis_destroy", "fsim_basis_nbf", "fsim_basis_nshell",
            "fsim_basis_pair_counts", "fsim_enuc", "fsim_onee", "fsim_schwarz", "fsim_fock_opts_default",
-           "fsim_fock_build", "fsim_last_quartet_count", "fsim_last_class_times", "fsim_eri_quartets", "fsim_eri_dump",
+           "fsim_fock_build", "fsim_fock_build_noalloc", "fsim_last_quartet_count", "fsim_last_class_times", "fsim_eri_quartets", "fsim_eri_dump",
            "fsim_scf_opts_default", "fsim_scf", "fsim_last_error"]
 
 
@@ -96,6 +96,7 @@ def load():
     L.fsim_fock_opts_default.argtypes = [C.POINTER(fsim_fock_opts)]
     L.fsim_fock_opts_default.restype = None
     L.fsim_fock_build.argtypes = [vp, vp, vp, vp, C.POINTER(fsim_fock_opts)]
+    L.fsim_fock_build_noalloc.argtypes = [vp, vp, vp, vp, C.POINTER(fsim_fock_opts)]
     L.fsim_last_quartet_count.argtypes = [vp]
     L.fsim_last_quartet_count.restype = C.c_longlong
     L.fsim_last_class_times.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_longlong), ip]
