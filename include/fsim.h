@@ -148,6 +148,21 @@ int fsim_fock_build(fsim_basis* b, const double* D, double* J, double* K, const 
  */
 int fsim_fock_build_noalloc(fsim_basis* b, const double* D, double* J, double* K, const fsim_fock_opts* opts);
 
+/*
+ * Autotuner for the Fock-build launches of this basis and these options
+ * (screening, precision, shard): for every class pair it times each launch
+ * shape on the device -- the unrolled per-class kernel with the bra primitive
+ * pairs split over 1, 3 or 9 threads (tiles of 128, 42 or 14 kets per CTA),
+ * in mixed precision also its chunk-warp form (one warp per ket-component
+ * chunk, tiles of 32 kets), and the warp-cooperative kernel (4 kets per CTA)
+ * -- and keeps the fastest in the basis' cached plan, which later
+ * fsim_fock_build calls with the same options use.  choice (36 entries,
+ * optional): chosen split, -2 chunk-warp, -1 cooperative kernel, 0 for class
+ * pairs without work; best_ms (36, optional):
+ * its median time.  Index X*6+Y as in fsim_last_class_times.
+ */
+int fsim_autotune(fsim_basis* b, const fsim_fock_opts* opts, int* choice, float* best_ms);
+
 /* Unique shell quartets the last fsim_fock_build evaluated (after screening). */
 long long fsim_last_quartet_count(const fsim_basis* b);
 
@@ -216,6 +231,35 @@ typedef struct {
  * min eig(S) < 1e-10.
  */
 int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res);
+
+/*
+ * Batched Fock builds for many molecules of uneven size (the paper's
+ * J/K construction, Sec. 3.2, for a set of molecules at once).  A batch binds
+ * nmol bases to fixed device buffers D[m] -> J[m], K[m] (each nbf_m^2 FP64,
+ * owned by the caller, which must outlive the batch) and concatenates their
+ * screened work so that every class pair is ONE persistent launch over all
+ * molecules.  fsim_batch_fock runs one build of every molecule flagged in
+ * `active` (host array of nmol ints, NULL = all); with use_graph the whole
+ * launch sequence of a precision is captured into a CUDA graph on first use
+ * and replayed afterwards.  Screening tau and the stream come from opts.
+ * Schwarz bounds and plans are built at creation (allocates).
+ */
+typedef struct fsim_batch fsim_batch;
+int fsim_batch_create(fsim_basis* const* bases, int nmol, const fsim_fock_opts* opts, const double* const* D,
+                      double* const* J, double* const* K, fsim_batch** out);
+int fsim_batch_fock(fsim_batch* batch, int precision, const int* active, int use_graph);
+void fsim_batch_destroy(fsim_batch* batch);
+
+/*
+ * Restricted Hartree-Fock for nmol molecules in lockstep (Sec. 3.2, 3.2.1):
+ * per iteration one batched Fock build (graph replay; FP64 and/or mixed
+ * group as each molecule's state requires) and the per-molecule FP64 linear
+ * algebra spread over several streams; converged molecules drop out.  Same
+ * options and per-molecule semantics as fsim_scf (core-H guess only; each
+ * molecule's electron count is its nuclear charge).  results: nmol entries;
+ * time_s is the time at which that molecule converged.
+ */
+int fsim_scf_batched(fsim_basis* const* bases, int nmol, const fsim_scf_opts* opts, fsim_scf_result* results);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* fsim_last_error(void);

@@ -69,7 +69,7 @@ template <int LA, int LB>
 __global__ void pair_data_kernel(int n, int ppmax, const int4* __restrict__ idx, const double* __restrict__ cen,
                                  const double* __restrict__ alpha, const double* __restrict__ coef,
                                  const int* __restrict__ nprim, double* __restrict__ pd64,
-                                 float* __restrict__ pd32, double4* __restrict__ pq64, float4* __restrict__ pq32) {
+                                 float* __restrict__ pd32, double4_32a* __restrict__ pq64, float4* __restrict__ pq32) {
   using PC = PairCls<LA, LB>;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * ppmax) return;
@@ -83,7 +83,7 @@ __global__ void pair_data_kernel(int n, int ppmax, const int4* __restrict__ idx,
     pd32[f * fs + (size_t)k * n + j] = (float)v;
   };
   if (k >= Ka * Kb) {
-    pq64[(size_t)k * n + j] = make_double4(1.0, 0.0, 0.0, 0.0);
+    pq64[(size_t)k * n + j] = make_double4_32a(1.0, 0.0, 0.0, 0.0);
     pq32[(size_t)k * n + j] = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
     put(0, 1.0);
     put(1, 0.0); put(2, 0.0); put(3, 0.0);
@@ -127,7 +127,7 @@ __global__ void pair_data_kernel(int n, int ppmax, const int4* __restrict__ idx,
                        4.18251339837959907596 /* pi^{5/4} */ / p;
   put(0, p);
   put(1, P[0]); put(2, P[1]); put(3, P[2]);
-  pq64[(size_t)k * n + j] = make_double4(p, P[0], P[1], P[2]);
+  pq64[(size_t)k * n + j] = make_double4_32a(p, P[0], P[1], P[2]);
   pq32[(size_t)k * n + j] = make_float4((float)p, (float)P[0], (float)P[1], (float)P[2]);
   static_for<PC::NC>([&](auto Aa) {
     constexpr int ac = decltype(Aa)::value;
@@ -144,7 +144,7 @@ __global__ void pair_data_kernel(int n, int ppmax, const int4* __restrict__ idx,
 }
 
 static cudaError_t launch_pair_data(int cls, int n, int ppmax, const int4* idx, const fsim_basis* b, double* pd64,
-                                    float* pd32, double4* pq64, float4* pq32) {
+                                    float* pd32, double4_32a* pq64, float4* pq32) {
   const int total = n * ppmax, th = 128, bl = (total + th - 1) / th;
   if (total == 0) return cudaSuccess;
   switch (cls) {

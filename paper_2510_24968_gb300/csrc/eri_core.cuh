@@ -34,7 +34,7 @@ template <typename Real>
 struct Vec4;
 template <>
 struct Vec4<double> {
-  using type = double4;
+  using type = double4_32a;
 };
 template <>
 struct Vec4<float> {
@@ -51,18 +51,30 @@ struct PairView {
   const typename Vec4<Real>::type* __restrict__ pq;  // (p, Px, Py, Pz) at [pp][pair]
 };
 
+// Everything a work item needs about its molecule.
 template <typename Real>
-struct JKParams {
+struct JKMol {
   PairView<Real> bra, ket;
   const int* __restrict__ tile_prefix;  // [nbra + 1] cumulative ket tiles per bra
   const int* __restrict__ ket_count;    // [nbra] screened ket prefix length per bra
-  int nitems;
-  int same;                             // bra class == ket class
-  int psplit;                           // bra primitive pairs split over this many threads
   int N;
   const Real* __restrict__ D;           // density, N x N, in the working precision
   double* J;                            // accumulators (FP64), N x N
   double* K;
+};
+
+template <typename Real>
+struct JKParams {
+  JKMol<Real> one;                      // single molecule (nmol == 0)
+  const JKMol<Real>* __restrict__ mols; // batched: one entry per molecule
+  const int* __restrict__ mol_prefix;   // batched: [nmol + 1] cumulative work items
+  const int* __restrict__ active;       // batched, optional: molecules whose items run
+  const int* __restrict__ mol_ids;      // batched: table entry -> index into active
+  int nmol;
+  int nitems;                           // total work items
+  int same;                             // bra class == ket class
+  int psplit;                           // bra primitive pairs split over this many threads
+  int bra_ppmax;                        // largest bra primitive-pair count (shared-memory size)
   const Real* __restrict__ boys;
   float boys64_T;                       // FP32 path: Boys in FP64 at T >= this (infinity = never)
 };
@@ -247,45 +259,54 @@ __global__ void __launch_bounds__(kJKThreads) jk_kernel(JKParams<Real> P) {
 
   for (int x = threadIdx.x; x < BR * BK; x += blockDim.x)
     sBoys[x] = P.boys[(x / BK) * kBoysCols + L + x % BK];
-  const int N = P.N;
   const int ps = P.psplit;
   const int tq = blockDim.x / ps;
   const int q = threadIdx.x / ps, bs = threadIdx.x % ps;
   const int lane = threadIdx.x & 31;
 
   for (int item = blockIdx.x; item < P.nitems; item += gridDim.x) {
-    const int i = find_bra(P.tile_prefix, P.bra.n, item);
-    const int tile = item - __ldg(P.tile_prefix + i);
-    const int4 bi = P.bra.idx[i];
-    const int nppb = P.bra.npp[i];
+    int litem = item;
+    const JKMol<Real>* Mp = &P.one;
+    if (P.nmol > 0) {
+      const int m = find_bra(P.mol_prefix, P.nmol, item);
+      if (P.active && !__ldg(P.active + __ldg(P.mol_ids + m))) continue;  // uniform per CTA: skip a converged molecule
+      Mp = P.mols + m;
+      litem = item - __ldg(P.mol_prefix + m);
+    }
+    const JKMol<Real> M = *Mp;
+    const int N = M.N;
+    const int i = find_bra(M.tile_prefix, M.bra.n, litem);
+    const int tile = litem - __ldg(M.tile_prefix + i);
+    const int4 bi = M.bra.idx[i];
+    const int nppb = M.bra.npp[i];
     __syncthreads();  // previous item done with the bra buffers
     for (int x = threadIdx.x; x < nppb * NFB; x += blockDim.x) {
       const int pp = x / NFB, f = x % NFB;
-      sbra[x] = P.bra.pd[((size_t)f * P.bra.ppmax + pp) * P.bra.n + i];
+      sbra[x] = M.bra.pd[((size_t)f * M.bra.ppmax + pp) * M.bra.n + i];
     }
-    for (int x = threadIdx.x; x < BC::NC; x += blockDim.x) sDab[x] = P.D[(size_t)(bi.x + x / BC::NB) * N + bi.y + x % BC::NB];
+    for (int x = threadIdx.x; x < BC::NC; x += blockDim.x) sDab[x] = M.D[(size_t)(bi.x + x / BC::NB) * N + bi.y + x % BC::NB];
     __syncthreads();
 
     const int j = tile * tq + q;
     Real jb[BC::NC];  // this thread's part of J_acc for the bra block
 #pragma unroll
     for (int a = 0; a < BC::NC; ++a) jb[a] = Real(0);
-    if (q < tq && j < __ldg(P.ket_count + i)) {
-      const int4 ki = P.ket.idx[j];
-      const int nppk = P.ket.npp[j];
+    if (q < tq && j < __ldg(M.ket_count + i)) {
+      const int4 ki = M.ket.idx[j];
+      const int nppk = M.ket.npp[j];
       const Real deg = Real((bi.z == bi.w ? 1 : 2) * (ki.z == ki.w ? 1 : 2) * ((P.same && i == j) ? 1 : 2));
       auto bra = [&](int f, int pp) -> Real { return sbra[pp * NFB + f]; };
       static_for<KetChunks<KC, CS>::NCH>([&](auto Ch) {
         constexpr int ch = decltype(Ch)::value;
         Real out[BC::NC][CS];
-        quartet_chunk<Real, LA, LB, LC, LD, CS, ch>(out, bra, nppb, bs, ps, P.ket, j, nppk, sBoys, BK, P.boys64_T);
+        quartet_chunk<Real, LA, LB, LC, LD, CS, ch>(out, bra, nppb, bs, ps, M.ket, j, nppk, sBoys, BK, P.boys64_T);
         // digestion (Eq. fock) of this chunk
 #pragma unroll
         for (int cs = 0; cs < CS; ++cs) {
           const int c = ch * CS + cs;
           const int lam = ki.x + c / KC::NB, sig = ki.y + c % KC::NB;
           // J_ket[la si] += sum_a D_ab v ; J_bra[a] += D_{la si} v
-          const Real Dls = P.D[(size_t)lam * N + sig];
+          const Real Dls = M.D[(size_t)lam * N + sig];
           Real jk = Real(0);
 #pragma unroll
           for (int a = 0; a < BC::NC; ++a) {
@@ -293,7 +314,7 @@ __global__ void __launch_bounds__(kJKThreads) jk_kernel(JKParams<Real> P) {
             jk = fma(sDab[a], v, jk);
             jb[a] = fma(Dls, v, jb[a]);
           }
-          atomicAdd(&P.J[(size_t)lam * N + sig], (double)jk);
+          atomicAdd(&M.J[(size_t)lam * N + sig], (double)jk);
           // K: (mu la) += D_nu si v ; (nu si) += D_mu la v ; (mu si) += D_nu la v ; (nu la) += D_mu si v
 #pragma unroll
           for (int ia = 0; ia < BC::NA; ++ia) {
@@ -303,11 +324,11 @@ __global__ void __launch_bounds__(kJKThreads) jk_kernel(JKParams<Real> P) {
             for (int ib = 0; ib < BC::NB; ++ib) {
               const int nu = bi.y + ib;
               const Real v = deg * out[ia * BC::NB + ib][cs];
-              k1 = fma(P.D[(size_t)nu * N + sig], v, k1);
-              k3 = fma(P.D[(size_t)nu * N + lam], v, k3);
+              k1 = fma(M.D[(size_t)nu * N + sig], v, k1);
+              k3 = fma(M.D[(size_t)nu * N + lam], v, k3);
             }
-            atomicAdd(&P.K[(size_t)mu * N + lam], (double)k1);
-            atomicAdd(&P.K[(size_t)mu * N + sig], (double)k3);
+            atomicAdd(&M.K[(size_t)mu * N + lam], (double)k1);
+            atomicAdd(&M.K[(size_t)mu * N + sig], (double)k3);
           }
 #pragma unroll
           for (int ib = 0; ib < BC::NB; ++ib) {
@@ -317,11 +338,11 @@ __global__ void __launch_bounds__(kJKThreads) jk_kernel(JKParams<Real> P) {
             for (int ia = 0; ia < BC::NA; ++ia) {
               const int mu = bi.x + ia;
               const Real v = deg * out[ia * BC::NB + ib][cs];
-              k2 = fma(P.D[(size_t)mu * N + lam], v, k2);
-              k4 = fma(P.D[(size_t)mu * N + sig], v, k4);
+              k2 = fma(M.D[(size_t)mu * N + lam], v, k2);
+              k4 = fma(M.D[(size_t)mu * N + sig], v, k4);
             }
-            atomicAdd(&P.K[(size_t)nu * N + sig], (double)k2);
-            atomicAdd(&P.K[(size_t)nu * N + lam], (double)k4);
+            atomicAdd(&M.K[(size_t)nu * N + sig], (double)k2);
+            atomicAdd(&M.K[(size_t)nu * N + lam], (double)k4);
           }
         }
       });
@@ -341,7 +362,121 @@ __global__ void __launch_bounds__(kJKThreads) jk_kernel(JKParams<Real> P) {
     for (int x = threadIdx.x; x < BC::NC; x += blockDim.x) {
       double v = 0.0;
       for (int w = 0; w < NWARP; ++w) v += (double)sJw[w * BC::NC + x];
-      atomicAdd(&P.J[(size_t)(bi.x + x / BC::NB) * N + bi.y + x % BC::NB], v);
+      atomicAdd(&M.J[(size_t)(bi.x + x / BC::NB) * N + bi.y + x % BC::NB], v);
+    }
+  }
+}
+
+// Chunk-warp variant for classes whose ket components span several register
+// chunks: a work item is (bra pair, tile of 32 kets, group of 4 chunks); warp w
+// of the CTA computes chunk 4*group + w for the 32 kets (lane = ket), so the
+// chunk index is uniform per warp and each warp runs the compile-time code of
+// its own chunk.  Parallelism grows by the number of chunks.
+constexpr int kCWKets = 32;
+constexpr int kCWWarps = kJKThreads / 32;
+
+template <typename Real, int LA, int LB, int LC, int LD, int CS>
+__global__ void __launch_bounds__(kJKThreads) jk_kernel_cw(JKParams<Real> P) {
+  using BC = PairCls<LA, LB>;
+  using KC = PairCls<LC, LD>;
+  constexpr int L = LA + LB + LC + LD;
+  constexpr int NFB = 4 + BC::NNZ;
+  constexpr int NCH = KetChunks<KC, CS>::NCH;
+  constexpr int NGRP = (NCH + kCWWarps - 1) / kCWWarps;
+  constexpr int BK = Boys<Real>::K, BR = Boys<Real>::NROW;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sBoys = reinterpret_cast<Real*>(smem_raw);
+  Real* sDab = reinterpret_cast<Real*>(smem_raw + (jk_boys_smem<Real>() + 15) / 16 * 16);
+  Real* sJw = sDab + BC::NC;
+  Real* sbra = sJw + kCWWarps * BC::NC;
+  for (int x = threadIdx.x; x < BR * BK; x += blockDim.x) sBoys[x] = P.boys[(x / BK) * kBoysCols + L + x % BK];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int item = blockIdx.x; item < P.nitems; item += gridDim.x) {
+    const JKMol<Real>& M = P.one;
+    const int N = M.N;
+    const int grp = item % NGRP, titem = item / NGRP;
+    const int i = find_bra(M.tile_prefix, M.bra.n, titem);
+    const int tile = titem - __ldg(M.tile_prefix + i);
+    const int4 bi = M.bra.idx[i];
+    const int nppb = M.bra.npp[i];
+    __syncthreads();
+    for (int x = threadIdx.x; x < nppb * NFB; x += blockDim.x) {
+      const int pp = x / NFB, f = x % NFB;
+      sbra[x] = M.bra.pd[((size_t)f * M.bra.ppmax + pp) * M.bra.n + i];
+    }
+    for (int x = threadIdx.x; x < BC::NC; x += blockDim.x) sDab[x] = M.D[(size_t)(bi.x + x / BC::NB) * N + bi.y + x % BC::NB];
+    __syncthreads();
+    const int j = tile * kCWKets + lane;
+    const int mych = grp * kCWWarps + warp;
+    Real jb[BC::NC];
+#pragma unroll
+    for (int a = 0; a < BC::NC; ++a) jb[a] = Real(0);
+    if (mych < NCH && j < __ldg(M.ket_count + i)) {
+      const int4 ki = M.ket.idx[j];
+      const int nppk = M.ket.npp[j];
+      const Real deg = Real((bi.z == bi.w ? 1 : 2) * (ki.z == ki.w ? 1 : 2) * ((P.same && i == j) ? 1 : 2));
+      auto bra = [&](int f, int pp) -> Real { return sbra[pp * NFB + f]; };
+      static_for<NCH>([&](auto Ch) {
+        constexpr int ch = decltype(Ch)::value;
+        if (ch != mych) return;  // warp-uniform
+        Real out[BC::NC][CS];
+        quartet_chunk<Real, LA, LB, LC, LD, CS, ch>(out, bra, nppb, 0, 1, M.ket, j, nppk, sBoys, BK, P.boys64_T);
+#pragma unroll
+        for (int cs = 0; cs < CS; ++cs) {
+          const int c = ch * CS + cs;
+          const int lam = ki.x + c / KC::NB, sig = ki.y + c % KC::NB;
+          const Real Dls = M.D[(size_t)lam * N + sig];
+          Real jk = Real(0);
+#pragma unroll
+          for (int a = 0; a < BC::NC; ++a) {
+            const Real v = deg * out[a][cs];
+            jk = fma(sDab[a], v, jk);
+            jb[a] = fma(Dls, v, jb[a]);
+          }
+          atomicAdd(&M.J[(size_t)lam * N + sig], (double)jk);
+#pragma unroll
+          for (int ia = 0; ia < BC::NA; ++ia) {
+            const int mu = bi.x + ia;
+            Real k1 = Real(0), k3 = Real(0);
+#pragma unroll
+            for (int ib = 0; ib < BC::NB; ++ib) {
+              const int nu = bi.y + ib;
+              const Real v = deg * out[ia * BC::NB + ib][cs];
+              k1 = fma(M.D[(size_t)nu * N + sig], v, k1);
+              k3 = fma(M.D[(size_t)nu * N + lam], v, k3);
+            }
+            atomicAdd(&M.K[(size_t)mu * N + lam], (double)k1);
+            atomicAdd(&M.K[(size_t)mu * N + sig], (double)k3);
+          }
+#pragma unroll
+          for (int ib = 0; ib < BC::NB; ++ib) {
+            const int nu = bi.y + ib;
+            Real k2 = Real(0), k4 = Real(0);
+#pragma unroll
+            for (int ia = 0; ia < BC::NA; ++ia) {
+              const int mu = bi.x + ia;
+              const Real v = deg * out[ia * BC::NB + ib][cs];
+              k2 = fma(M.D[(size_t)mu * N + lam], v, k2);
+              k4 = fma(M.D[(size_t)mu * N + sig], v, k4);
+            }
+            atomicAdd(&M.K[(size_t)nu * N + sig], (double)k2);
+            atomicAdd(&M.K[(size_t)nu * N + lam], (double)k4);
+          }
+        }
+      });
+    }
+#pragma unroll
+    for (int a = 0; a < BC::NC; ++a) {
+      Real v = jb[a];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) sJw[warp * BC::NC + a] = v;
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < BC::NC; x += blockDim.x) {
+      double v = 0.0;
+      for (int w = 0; w < kCWWarps; ++w) v += (double)sJw[w * BC::NC + x];
+      atomicAdd(&M.J[(size_t)(bi.x + x / BC::NB) * N + bi.y + x % BC::NB], v);
     }
   }
 }

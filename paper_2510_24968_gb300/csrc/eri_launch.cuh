@@ -37,7 +37,7 @@ cudaError_t launch_jk(const JKParams<Real>& p, cudaStream_t s) {
   using BC = PairCls<LA, LB>;
   auto k = jk_kernel<Real, LA, LB, LC, LD, CS>;
   const size_t smem = (jk_boys_smem<Real>() + 15) / 16 * 16 + (1 + kJKThreads / 32) * BC::NC * sizeof(Real) +
-                      (size_t)p.bra.ppmax * (4 + BC::NNZ) * sizeof(Real);
+                      (size_t)p.bra_ppmax * (4 + BC::NNZ) * sizeof(Real);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (p.nitems == 0) return cudaSuccess;
@@ -49,6 +49,32 @@ cudaError_t launch_jk(const JKParams<Real>& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Chunk-warp launch (FP32 classes with several ket chunks); nitems counts
+// (bra, 32-ket tile) pairs, the launch multiplies by the chunk groups.
+template <typename Real, int X, int Y>
+cudaError_t launch_jk_cw(const JKParams<Real>& p, cudaStream_t s) {
+  constexpr int LA = pair_cls_la(X), LB = pair_cls_lb(X), LC = pair_cls_la(Y), LD = pair_cls_lb(Y);
+  constexpr int CS = chunk_size<Real>(X, Y);
+  using BC = PairCls<LA, LB>;
+  using KC = PairCls<LC, LD>;
+  constexpr int NGRP = (KetChunks<KC, CS>::NCH + kCWWarps - 1) / kCWWarps;
+  auto k = jk_kernel_cw<Real, LA, LB, LC, LD, CS>;
+  const size_t smem = (jk_boys_smem<Real>() + 15) / 16 * 16 + (1 + kCWWarps) * BC::NC * sizeof(Real) +
+                      (size_t)p.bra_ppmax * (4 + BC::NNZ) * sizeof(Real);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (p.nitems == 0) return cudaSuccess;
+  JKParams<Real> q = p;
+  q.nitems = p.nitems * NGRP;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kJKThreads, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = std::min(q.nitems, std::max(1, occ) * device_sm_count());
+  k<<<grid, kJKThreads, smem, s>>>(q);
+  return cudaGetLastError();
+}
+
+#define FSIM_INSTANTIATE_CW(X, Y) template cudaError_t launch_jk_cw<float, X, Y>(const JKParams<float>&, cudaStream_t);
 #define FSIM_INSTANTIATE_JK(T, X, Y) template cudaError_t launch_jk<T, X, Y>(const JKParams<T>&, cudaStream_t);
 
 }  // namespace fsim

@@ -69,6 +69,41 @@ static cudaError_t dispatch_jk(int X, int Y, const JKParams<Real>& p, cudaStream
   return cudaErrorInvalidValue;
 }
 
+bool has_cw_variant(int X, int Y) {
+  switch (X * 8 + Y) {
+    case 18:
+    case 34:
+    case 35:
+    case 36:
+    case 41:
+    case 42:
+    case 43:
+    case 44:
+    case 45:
+      return true;
+  }
+  return false;
+}
+
+// Chunk-warp launches exist for FP32 classes with several ket chunks only.
+template <typename Real>
+static cudaError_t dispatch_jk_cw(int X, int Y, const JKParams<Real>& p, cudaStream_t s) {
+  if constexpr (std::is_same<Real, float>::value) {
+    switch (X * 8 + Y) {
+    case 18: return launch_jk_cw<float, 2, 2>(p, s);
+    case 34: return launch_jk_cw<float, 4, 2>(p, s);
+    case 35: return launch_jk_cw<float, 4, 3>(p, s);
+    case 36: return launch_jk_cw<float, 4, 4>(p, s);
+    case 41: return launch_jk_cw<float, 5, 1>(p, s);
+    case 42: return launch_jk_cw<float, 5, 2>(p, s);
+    case 43: return launch_jk_cw<float, 5, 3>(p, s);
+    case 44: return launch_jk_cw<float, 5, 4>(p, s);
+    case 45: return launch_jk_cw<float, 5, 5>(p, s);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
 int run_list(fsim_basis* b, int X, int Y, const std::vector<int2>& items, double* d_out, int precision,
              cudaStream_t s) {
   if (precision != FSIM_FP64) {
@@ -102,10 +137,61 @@ int run_list(fsim_basis* b, int X, int Y, const std::vector<int2>& items, double
   return FSIM_OK;
 }
 
-// Screened plan for (tau, shard); cached on the basis.
-int get_plan(fsim_basis* b, double tau, int shard, int nshards, int precision, FockPlan** out) {
+// Screened ket counts of class pair (X, Y): count[i] = kets of bra i with
+// Q_i Q_j >= tau (class Y sorted by Q descending), cut at j <= i when X == Y.
+static long long screened_counts(const fsim_basis* b, int X, int Y, double tau, int shard, int nshards,
+                                 std::vector<int>& count) {
+  const DevClass& CX = b->cls[X];
+  const DevClass& CY = b->cls[Y];
+  count.assign(CX.n, 0);
+  long long nq = 0;
+  for (int i = 0; i < CX.n; ++i) {
+    int cnt;
+    if (tau > 0.0) {
+      const double qi = CX.h_Q[i];
+      int lo = 0, hi = CY.n;
+      while (lo < hi) {
+        const int mid = (lo + hi) / 2;
+        if (qi * CY.h_Q[mid] >= tau) lo = mid + 1; else hi = mid;
+      }
+      cnt = lo;
+    } else {
+      cnt = CY.n;
+    }
+    if (X == Y) cnt = std::min(cnt, i + 1);
+    if (nshards > 1 && (i % nshards) != shard) cnt = 0;
+    count[i] = cnt;
+    nq += cnt;
+  }
+  return nq;
+}
+
+// (Re)build the device work list of one class pair for a launch shape:
+// psplit threads per quartet on the unrolled kernel, or the cooperative kernel.
+int set_class_plan(fsim_basis* b, int X, int Y, const std::vector<int>& count, int psplit, int coop,
+                   ClassPairPlan& cp, int cw) {
+  const DevClass& CX = b->cls[X];
+  cp.cw = (cw && !coop) ? 1 : 0;
+  cp.psplit = (coop || cp.cw) ? 1 : psplit;
+  cp.coop = coop;
+  cp.tq = coop ? kCoopWarps : (cp.cw ? kCWKets : kJKThreads / cp.psplit);
+  std::vector<int> prefix(CX.n + 1, 0);
+  for (int i = 0; i < CX.n; ++i) prefix[i + 1] = prefix[i] + (count[i] + cp.tq - 1) / cp.tq;
+  cp.nitems = prefix[CX.n];
+  if (!cp.d_prefix) FSIM_TRY(dev_alloc(&cp.d_prefix, CX.n + 1));
+  if (!cp.d_count) FSIM_TRY(dev_alloc(&cp.d_count, CX.n));
+  FSIM_CK(cudaMemcpy(cp.d_prefix, prefix.data(), sizeof(int) * (CX.n + 1), cudaMemcpyHostToDevice));
+  FSIM_CK(cudaMemcpy(cp.d_count, count.data(), sizeof(int) * CX.n, cudaMemcpyHostToDevice));
+  return FSIM_OK;
+}
+
+// Screened plan for (tau, shard, precision, psplit_force); cached on the basis.
+// psplit_force = 0: class pairs with few quartets split the bra primitive pairs
+// over several threads so that one launch still covers the device.
+int get_plan(fsim_basis* b, double tau, int shard, int nshards, int precision, FockPlan** out, int psplit_force) {
   for (FockPlan* p : b->plans)
-    if (p->tau == tau && p->shard == shard && p->nshards == nshards && p->precision == precision) {
+    if (p->tau == tau && p->shard == shard && p->nshards == nshards && p->precision == precision &&
+        p->psplit_force == psplit_force) {
       *out = p;
       return FSIM_OK;
     }
@@ -114,53 +200,30 @@ int get_plan(fsim_basis* b, double tau, int shard, int nshards, int precision, F
   P->shard = shard;
   P->nshards = nshards;
   P->precision = precision;
+  P->psplit_force = psplit_force;
   b->plans.push_back(P);
   for (int X = 0; X < kNumPairCls; ++X)
     for (int Y = 0; Y <= X; ++Y) {
       ClassPairPlan& cp = P->cp[X][Y];
       const DevClass& CX = b->cls[X];
-      const DevClass& CY = b->cls[Y];
       cp.nbra = CX.n;
-      cp.psplit = 1;
+      if (CX.n == 0 || b->cls[Y].n == 0) continue;
+      std::vector<int> count;
+      cp.nquartets = screened_counts(b, X, Y, tau, shard, nshards, count);
       const int L = pair_cls_la(X) + pair_cls_lb(X) + pair_cls_la(Y) + pair_cls_lb(Y);
-      cp.coop = (precision == FSIM_FP64 && L >= kCoopMinL64) ? 1 : 0;
-      if (CX.n == 0 || CY.n == 0) continue;
-      std::vector<int> prefix(CX.n + 1, 0), count(CX.n, 0);
-      for (int i = 0; i < CX.n; ++i) {
-        int cnt;
-        if (tau > 0.0) {
-          // kets sorted by Q descending: count of j with Q_i Q_j >= tau
-          const double qi = CX.h_Q[i];
-          int lo = 0, hi = CY.n;
-          while (lo < hi) {
-            const int mid = (lo + hi) / 2;
-            if (qi * CY.h_Q[mid] >= tau) lo = mid + 1; else hi = mid;
-          }
-          cnt = lo;
+      const int coop = (precision == FSIM_FP64 && L >= kCoopMinL64) ? 1 : 0;
+      int ps = 1, cw = 0;
+      if (!coop) {
+        if (psplit_force > 0) {
+          ps = std::min(psplit_force, CX.ppmax);
         } else {
-          cnt = CY.n;
+          const long long target = (long long)device_sm_count() * 2 * kJKThreads;
+          for (int c : {3, 9})
+            if (cp.nquartets * ps < target && c <= CX.ppmax) ps = c;
         }
-        if (X == Y) cnt = std::min(cnt, i + 1);
-        if (nshards > 1 && (i % nshards) != shard) cnt = 0;
-        count[i] = cnt;
-        cp.nquartets += cnt;
       }
-      // class pairs with few quartets split the bra primitive pairs over
-      // several threads so that the launch still covers the device
-      if (!cp.coop) {
-        const long long target = (long long)device_sm_count() * 2 * kJKThreads;
-        for (int ps : {3, 9})
-          if (cp.nquartets * cp.psplit < target && ps <= CX.ppmax) cp.psplit = ps;
-      }
-      cp.tq = cp.coop ? kCoopWarps : kJKThreads / cp.psplit;
-      const int tq = cp.tq;
-      for (int i = 0; i < CX.n; ++i) prefix[i + 1] = prefix[i] + (count[i] + tq - 1) / tq;
-      cp.nitems = prefix[CX.n];
+      FSIM_TRY(set_class_plan(b, X, Y, count, ps, coop, cp, cw));
       P->nquartets += cp.nquartets;
-      FSIM_TRY(dev_alloc(&cp.d_prefix, CX.n + 1));
-      FSIM_TRY(dev_alloc(&cp.d_count, CX.n));
-      FSIM_CK(cudaMemcpy(cp.d_prefix, prefix.data(), sizeof(int) * (CX.n + 1), cudaMemcpyHostToDevice));
-      FSIM_CK(cudaMemcpy(cp.d_count, count.data(), sizeof(int) * CX.n, cudaMemcpyHostToDevice));
     }
   *out = P;
   return FSIM_OK;
@@ -180,7 +243,7 @@ __global__ void symmetrize_kernel(const double* __restrict__ Ja, const double* _
   K[(size_t)r * N + c] = 0.125 * (Ka[(size_t)r * N + c] + Ka[(size_t)c * N + r]);
 }
 
-static int ensure_scratch(fsim_basis* b) {
+int ensure_scratch(fsim_basis* b) {
   const size_t n2 = (size_t)b->nbf * b->nbf;
   if (!b->d_Jacc) FSIM_TRY(dev_alloc(&b->d_Jacc, n2));
   if (!b->d_Kacc) FSIM_TRY(dev_alloc(&b->d_Kacc, n2));
@@ -221,9 +284,16 @@ static int launch_all(fsim_basis* b, FockPlan* plan, const Real* Dr, float boys6
         p.boys64_T = boys64_T;
         e = launch_coop<Real>(p, cp.nitems, s);
       } else {
-        JKParams<Real> p{b->cls[X].view<Real>(), b->cls[Y].view<Real>(), cp.d_prefix, cp.d_count, cp.nitems,
-                         X == Y ? 1 : 0, cp.psplit, b->nbf, Dr, b->d_Jacc, b->d_Kacc, boys, boys64_T};
-        e = dispatch_jk<Real>(X, Y, p, s);
+        JKParams<Real> p{};
+        p.one = JKMol<Real>{b->cls[X].view<Real>(), b->cls[Y].view<Real>(), cp.d_prefix, cp.d_count, b->nbf, Dr,
+                            b->d_Jacc, b->d_Kacc};
+        p.nitems = cp.nitems;
+        p.same = X == Y ? 1 : 0;
+        p.psplit = cp.psplit;
+        p.bra_ppmax = b->cls[X].ppmax;
+        p.boys = boys;
+        p.boys64_T = boys64_T;
+        e = cp.cw ? dispatch_jk_cw<Real>(X, Y, p, s) : dispatch_jk<Real>(X, Y, p, s);
       }
       if (e != cudaSuccess) {
         set_error("J/K kernel (%d|%d): %s", X, Y, cudaGetErrorString(e));
@@ -252,7 +322,7 @@ int fock_build_device(fsim_basis* b, const double* dD, double* dJ, double* dK, c
   FSIM_TRY(ensure_schwarz(b));
   FSIM_TRY(ensure_scratch(b));
   FockPlan* plan = nullptr;
-  FSIM_TRY(get_plan(b, o.schwarz_tau, o.shard, o.nshards, o.precision, &plan));
+  FSIM_TRY(get_plan(b, o.schwarz_tau, o.shard, o.nshards, o.precision, &plan, 0));
   const int N = b->nbf;
   const size_t n2 = (size_t)N * N;
   if (o.timing && !b->ev_ok) {
@@ -531,9 +601,16 @@ static int launch_all_into(fsim_basis* b, FockPlan* plan, const Real* Dr, float 
         p.boys64_T = boys64_T;
         e = launch_coop<Real>(p, cp.nitems, s);
       } else {
-        JKParams<Real> p{b->cls[X].view<Real>(), b->cls[Y].view<Real>(), cp.d_prefix, cp.d_count, cp.nitems,
-                         X == Y ? 1 : 0, cp.psplit, b->nbf, Dr, Jacc, Kacc, boys, boys64_T};
-        e = dispatch_jk<Real>(X, Y, p, s);
+        JKParams<Real> p{};
+        p.one = JKMol<Real>{b->cls[X].view<Real>(), b->cls[Y].view<Real>(), cp.d_prefix, cp.d_count, b->nbf, Dr,
+                            Jacc, Kacc};
+        p.nitems = cp.nitems;
+        p.same = X == Y ? 1 : 0;
+        p.psplit = cp.psplit;
+        p.bra_ppmax = b->cls[X].ppmax;
+        p.boys = boys;
+        p.boys64_T = boys64_T;
+        e = cp.cw ? dispatch_jk_cw<Real>(X, Y, p, s) : dispatch_jk<Real>(X, Y, p, s);
       }
       if (e != cudaSuccess) {
         set_error("J/K kernel (%d|%d): %s", X, Y, cudaGetErrorString(e));
@@ -563,7 +640,8 @@ int fock_build_into(fsim_basis* b, const double* dD, double* dJ, double* dK, con
   }
   FockPlan* plan = nullptr;
   for (FockPlan* p : b->plans)
-    if (p->tau == o.schwarz_tau && p->shard == o.shard && p->nshards == o.nshards && p->precision == o.precision)
+    if (p->tau == o.schwarz_tau && p->shard == o.shard && p->nshards == o.nshards && p->precision == o.precision &&
+        p->psplit_force == 0)
       plan = p;
   if (!plan) {
     set_error("no screening plan for tau %g, shard %d/%d, precision %d: run fsim_fock_build once with the same "
@@ -591,3 +669,140 @@ int fock_build_into(fsim_basis* b, const double* dD, double* dJ, double* dK, con
 }
 
 }  // namespace fsim
+
+namespace fsim {
+
+// One class pair's launch with an explicit plan entry (autotuner).
+template <typename Real>
+static cudaError_t launch_cp(fsim_basis* b, int X, int Y, const ClassPairPlan& cp, const Real* Dr, double* Jacc,
+                             double* Kacc, float b64, cudaStream_t s) {
+  const Real* boys = std::is_same<Real, double>::value ? (const Real*)b->d_boys64 : (const Real*)b->d_boys32;
+  if (cp.nitems == 0) return cudaSuccess;
+  if (cp.coop) {
+    CoopParams<Real> p{};
+    p.bra = b->cls[X].view<Real>();
+    p.ket = b->cls[Y].view<Real>();
+    make_cls_desc(X, p.bd);
+    make_cls_desc(Y, p.kd);
+    p.same = X == Y ? 1 : 0;
+    p.tile_prefix = cp.d_prefix;
+    p.ket_count = cp.d_count;
+    p.tq = cp.tq;
+    p.nitems = cp.nitems;
+    p.N = b->nbf;
+    p.D = Dr;
+    p.J = Jacc;
+    p.K = Kacc;
+    p.boys = boys;
+    p.boys64_T = b64;
+    return launch_coop<Real>(p, cp.nitems, s);
+  }
+  JKParams<Real> p{};
+  p.one = JKMol<Real>{b->cls[X].view<Real>(), b->cls[Y].view<Real>(), cp.d_prefix, cp.d_count, b->nbf, Dr, Jacc, Kacc};
+  p.nitems = cp.nitems;
+  p.same = X == Y ? 1 : 0;
+  p.psplit = cp.psplit;
+  p.bra_ppmax = b->cls[X].ppmax;
+  p.boys = boys;
+  p.boys64_T = b64;
+  return cp.cw ? dispatch_jk_cw<Real>(X, Y, p, s) : dispatch_jk<Real>(X, Y, p, s);
+}
+
+template <typename Real>
+static int autotune_impl(fsim_basis* b, FockPlan* plan, const Real* Dr, float b64, cudaStream_t s, int* choice,
+                         float* best_ms) {
+  cudaEvent_t e0, e1;
+  FSIM_CK(cudaEventCreate(&e0));
+  FSIM_CK(cudaEventCreate(&e1));
+  int rc = FSIM_OK;
+  for (int X = 0; X < kNumPairCls && rc == FSIM_OK; ++X)
+    for (int Y = 0; Y <= X && rc == FSIM_OK; ++Y) {
+      ClassPairPlan& cp = plan->cp[X][Y];
+      const int ci = X * kNumPairCls + Y;
+      if (cp.nquartets == 0) continue;
+      std::vector<int> count;
+      screened_counts(b, X, Y, plan->tau, plan->shard, plan->nshards, count);
+      const int L = pair_cls_la(X) + pair_cls_lb(X) + pair_cls_la(Y) + pair_cls_lb(Y);
+      struct Cand {
+        int psplit, coop, cw;
+      };
+      std::vector<Cand> cands;
+      const bool unrolled_ok = !(std::is_same<Real, double>::value && L >= kCoopMinL64);
+      if (unrolled_ok)
+        for (int ps : {1, 3, 9})
+          if (ps <= b->cls[X].ppmax) cands.push_back({ps, 0, 0});
+      if (std::is_same<Real, float>::value && has_cw_variant(X, Y)) cands.push_back({1, 0, 1});
+      cands.push_back({1, 1, 0});
+      float best = 1e30f;
+      Cand win = cands[0];
+      ClassPairPlan tmp;
+      for (const Cand& c : cands) {
+        if ((rc = set_class_plan(b, X, Y, count, c.psplit, c.coop, tmp, c.cw)) != FSIM_OK) break;
+        float t[3];
+        cudaError_t e = launch_cp<Real>(b, X, Y, tmp, Dr, b->d_Jacc, b->d_Kacc, b64, s);  // warm-up
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+          cudaEventRecord(e0, s);
+          e = launch_cp<Real>(b, X, Y, tmp, Dr, b->d_Jacc, b->d_Kacc, b64, s);
+          cudaEventRecord(e1, s);
+          cudaEventSynchronize(e1);
+          cudaEventElapsedTime(&t[r], e0, e1);
+        }
+        if (e != cudaSuccess) {
+          set_error("autotune launch (%d|%d): %s", X, Y, cudaGetErrorString(e));
+          rc = FSIM_ECUDA;
+          break;
+        }
+        std::sort(t, t + 3);
+        if (t[1] < best) {
+          best = t[1];
+          win = c;
+        }
+      }
+      dev_free(tmp.d_prefix);
+      dev_free(tmp.d_count);
+      if (rc != FSIM_OK) break;
+      rc = set_class_plan(b, X, Y, count, win.psplit, win.coop, cp, win.cw);
+      if (choice) choice[ci] = win.coop ? -1 : (win.cw ? -2 : win.psplit);
+      if (best_ms) best_ms[ci] = best;
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc == FSIM_OK) plan->tuned = true;
+  return rc;
+}
+
+}  // namespace fsim
+
+extern "C" int fsim_autotune(fsim_basis* b, const fsim_fock_opts* opts, int* choice, float* best_ms) {
+  if (!b || !opts) {
+    set_error("fsim_autotune: null pointer");
+    return FSIM_EINVAL;
+  }
+  const fsim_fock_opts& o = *opts;
+  if (o.precision != FSIM_FP64 && o.precision != FSIM_MIXED) {
+    set_error("fsim_autotune: bad precision");
+    return FSIM_EINVAL;
+  }
+  if (choice)
+    for (int i = 0; i < 36; ++i) choice[i] = 0;
+  if (best_ms)
+    for (int i = 0; i < 36; ++i) best_ms[i] = -1.0f;
+  FSIM_TRY(ensure_schwarz(b));
+  FSIM_TRY(ensure_scratch(b));
+  FockPlan* plan = nullptr;
+  FSIM_TRY(get_plan(b, o.schwarz_tau, o.shard, o.nshards, o.precision, &plan, 0));
+  cudaStream_t s = (cudaStream_t)o.stream;
+  const size_t n2 = (size_t)b->nbf * b->nbf;
+  const float b64 = o.boys_fp64_T > 0.0 ? (float)o.boys_fp64_T : INFINITY;
+  if (o.precision == FSIM_MIXED) {
+    FSIM_CK(cudaMemsetAsync(b->d_D32, 0, n2 * sizeof(float), s));
+    return autotune_impl<float>(b, plan, b->d_D32, b64, s, choice, best_ms);
+  }
+  double* Dz = nullptr;
+  FSIM_TRY(dev_alloc(&Dz, n2));
+  FSIM_CK(cudaMemsetAsync(Dz, 0, n2 * sizeof(double), s));
+  int rc = autotune_impl<double>(b, plan, Dz, b64, s, choice, best_ms);
+  cudaStreamSynchronize(s);
+  dev_free(Dz);
+  return rc;
+}

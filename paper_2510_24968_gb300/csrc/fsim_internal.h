@@ -59,7 +59,7 @@ struct DevClass {
   int* npp = nullptr;
   double* pd64 = nullptr;   // [4 + nnz][ppmax][n]
   float* pd32 = nullptr;
-  double4* pq64 = nullptr;  // (p, P) at [ppmax][n]
+  double4_32a* pq64 = nullptr;  // (p, P) at [ppmax][n]
   float4* pq32 = nullptr;
   std::vector<int4> h_idx;  // host copy, same order
   std::vector<int> h_npp;
@@ -85,6 +85,7 @@ struct ClassPairPlan {
   long long nquartets = 0;
   int psplit = 1;
   int coop = 0;             // 1: warp-cooperative table-driven kernel
+  int cw = 0;               // 1: chunk-warp variant of the unrolled kernel (FP32)
   int tq = kJKThreads;      // kets per work item
   int* d_prefix = nullptr;  // [nbra + 1]
   int* d_count = nullptr;   // [nbra]
@@ -94,6 +95,8 @@ struct FockPlan {
   double tau = -1.0;
   int shard = 0, nshards = 1;
   int precision = 0;
+  int psplit_force = 0;
+  bool tuned = false;
   ClassPairPlan cp[kNumPairCls][kNumPairCls];
   long long nquartets = 0;
 };
@@ -101,6 +104,8 @@ struct FockPlan {
 // Kernel launchers (explicit instantiations in eri_inst_*.cu).
 template <typename Real, int X, int Y>
 cudaError_t launch_jk(const JKParams<Real>& p, cudaStream_t s);
+template <typename Real, int X, int Y>
+cudaError_t launch_jk_cw(const JKParams<Real>& p, cudaStream_t s);
 template <typename Real>
 struct CoopParams;
 template <typename Real>
@@ -152,7 +157,13 @@ struct fsim_basis {
 };
 
 namespace fsim {
-int get_plan(fsim_basis* b, double tau, int shard, int nshards, int precision, FockPlan** out);
+int get_plan(fsim_basis* b, double tau, int shard, int nshards, int precision, FockPlan** out, int psplit_force);
+int set_class_plan(fsim_basis* b, int X, int Y, const std::vector<int>& count, int psplit, int coop,
+                   ClassPairPlan& cp, int cw = 0);
+bool has_cw_variant(int X, int Y);
+int ensure_scratch(fsim_basis* b);
+int ensure_schwarz(fsim_basis* b);
+int device_sm_count();
 int build_pair_data(fsim_basis* b, int cls, const std::vector<int4>& order);
 int run_list(fsim_basis* b, int X, int Y, const std::vector<int2>& items, double* d_out, int precision,
              cudaStream_t s);

@@ -32,8 +32,9 @@ FSIM_GUESS_DENSITY = 1
 # every symbol declared in include/fsim.h
 EXPORTS = ["fsim_basis_create", "fsim_basis_destroy", "fsim_basis_nbf", "fsim_basis_nshell",
            "fsim_basis_pair_counts", "fsim_enuc", "fsim_onee", "fsim_schwarz", "fsim_fock_opts_default",
-           "fsim_fock_build", "fsim_fock_build_noalloc", "fsim_last_quartet_count", "fsim_last_class_times", "fsim_eri_quartets", "fsim_eri_dump",
-           "fsim_scf_opts_default", "fsim_scf", "fsim_last_error"]
+           "fsim_fock_build", "fsim_fock_build_noalloc", "fsim_autotune", "fsim_last_quartet_count", "fsim_last_class_times", "fsim_eri_quartets", "fsim_eri_dump",
+           "fsim_scf_opts_default", "fsim_scf", "fsim_batch_create", "fsim_batch_fock", "fsim_batch_destroy",
+           "fsim_scf_batched", "fsim_last_error"]
 
 
 class FsimError(RuntimeError):
@@ -97,6 +98,7 @@ def load():
     L.fsim_fock_opts_default.restype = None
     L.fsim_fock_build.argtypes = [vp, vp, vp, vp, C.POINTER(fsim_fock_opts)]
     L.fsim_fock_build_noalloc.argtypes = [vp, vp, vp, vp, C.POINTER(fsim_fock_opts)]
+    L.fsim_autotune.argtypes = [vp, C.POINTER(fsim_fock_opts), ip, C.POINTER(C.c_float)]
     L.fsim_last_quartet_count.argtypes = [vp]
     L.fsim_last_quartet_count.restype = C.c_longlong
     L.fsim_last_class_times.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_longlong), ip]
@@ -105,6 +107,12 @@ def load():
     L.fsim_scf_opts_default.argtypes = [C.POINTER(fsim_scf_opts)]
     L.fsim_scf_opts_default.restype = None
     L.fsim_scf.argtypes = [vp, C.POINTER(fsim_scf_opts), C.POINTER(fsim_scf_result)]
+    L.fsim_batch_create.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(fsim_fock_opts), C.POINTER(vp),
+                                    C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]
+    L.fsim_batch_fock.argtypes = [vp, C.c_int, ip, C.c_int]
+    L.fsim_batch_destroy.argtypes = [vp]
+    L.fsim_batch_destroy.restype = None
+    L.fsim_scf_batched.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(fsim_scf_opts), C.POINTER(fsim_scf_result)]
     L.fsim_last_error.restype = C.c_char_p
     _lib = L
     return L
@@ -220,6 +228,16 @@ class Basis:
         _check(load().fsim_fock_build(self.h, pD, pJ, pK, C.byref(o)))
         return J, K
 
+    def autotune(self, tau=1e-10, precision=FSIM_MIXED, stream=None, shard=0, nshards=1):
+        """Tune the launch shape of every class pair; returns {(X, Y): (choice, ms)}."""
+        o = fsim_fock_opts_default()
+        o.schwarz_tau, o.precision, o.shard, o.nshards = tau, precision, shard, nshards
+        o.stream = stream or 0
+        ch = (C.c_int * 36)()
+        ms = (C.c_float * 36)()
+        _check(load().fsim_autotune(self.h, C.byref(o), ch, ms))
+        return {(i // 6, i % 6): (ch[i], ms[i]) for i in range(36) if ch[i] != 0}
+
     def last_quartet_count(self) -> int:
         return load().fsim_last_quartet_count(self.h)
 
@@ -281,3 +299,57 @@ class Basis:
                 "quartets": r.quartets, "fp64_builds": r.fp64_builds, "mixed_builds": r.mixed_builds,
                 "energies": eh[:n].copy(), "times": th[:n].copy(), "D": Dout,
                 "guess_fallback": bool(r.guess_fallback)}
+
+
+class Batch:
+    """A set of bases bound to device buffers D[m] -> J[m], K[m] (CUDA torch tensors)."""
+
+    def __init__(self, bases, D, J, K, tau=1e-10, stream=None):
+        L = load()
+        n = len(bases)
+        self.bases, self._keep = bases, (D, J, K)
+        hb = (C.c_void_p * n)(*[b.h.value for b in bases])
+        hd = (C.c_void_p * n)(*[d.data_ptr() for d in D])
+        hj = (C.c_void_p * n)(*[x.data_ptr() for x in J])
+        hk = (C.c_void_p * n)(*[x.data_ptr() for x in K])
+        o = fsim_fock_opts_default()
+        o.schwarz_tau, o.ptr_mode, o.stream = tau, FSIM_PTR_DEVICE, stream or 0
+        h = C.c_void_p()
+        _check(L.fsim_batch_create(hb, n, C.byref(o), hd, hj, hk, C.byref(h)))
+        self.h = h
+
+    def fock(self, precision=FSIM_MIXED, active=None, use_graph=True):
+        act = None if active is None else (C.c_int * len(self.bases))(*[int(a) for a in active])
+        _check(load().fsim_batch_fock(self.h, precision, act, int(use_graph)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().fsim_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def scf_batched(bases, precision=FSIM_MIXED, tau=1e-10, max_iter=100, conv_dE=1e-10, conv_dD=1e-7, diis_size=8,
+                final_fp64=True, incremental=True, stream=None):
+    """Lockstep RHF of many molecules; returns a list of per-molecule dicts."""
+    n = len(bases)
+    o = fsim_scf_opts_default()
+    o.nelec = 0
+    o.max_iter, o.conv_dE, o.conv_dD, o.diis_size = max_iter, conv_dE, conv_dD, diis_size
+    o.fock.schwarz_tau, o.fock.precision = tau, precision
+    o.fock.stream = stream or 0
+    o.final_fp64, o.incremental = int(final_fp64), int(incremental)
+    res = (fsim_scf_result * n)()
+    hist = [np.full(max_iter, np.nan) for _ in range(n)]
+    for r, h in zip(res, hist):
+        r.e_hist = _dptr(h)
+    hb = (C.c_void_p * n)(*[b.h.value for b in bases])
+    rc = _check(load().fsim_scf_batched(hb, n, C.byref(o), res), allow=(FSIM_ENOCONV,))
+    return [{"e_total": r.e_total, "iters": r.iters, "converged": bool(r.converged), "time_s": r.time_s,
+             "fp64_builds": r.fp64_builds, "mixed_builds": r.mixed_builds, "rc": rc,
+             "energies": h[:r.iters].copy()} for r, h in zip(res, hist)]

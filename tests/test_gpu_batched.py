@@ -1,0 +1,120 @@
+"""Batched many-molecule path: one launch per class pair over all molecules,
+CUDA-graph replay, device-side active flags, lockstep SCF, autotuner.
+Compared against the single-molecule entry points (which are themselves
+parity-checked against the oracle in test_gpu_parity.py) and, for the SCF,
+against the oracle's energies."""
+import numpy as np
+import pytest
+
+from fsim_synth import batched_set, organic_cloud, water_cluster, workload
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_24968_gb300.build import build
+    build()
+
+
+def _mols():
+    return [workload("water"), water_cluster(2, geom_seed=7), organic_cloud(3, geom_seed=11),
+            organic_cloud(4, geom_seed=12), workload("water"), water_cluster(3, geom_seed=9)]
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_fock_matches_single_builds(use_graph):
+    from paper_2510_24968_gb300 import FSIM_FP64, FSIM_MIXED, Basis, Batch
+    mols = _mols()
+    bases = [Basis(m) for m in mols]
+    rng = np.random.default_rng(3)
+    D = []
+    for b in bases:
+        d = rng.standard_normal((b.nbf, b.nbf)) * 0.1
+        D.append(torch.from_numpy(d + d.T).cuda())
+    J = [torch.zeros_like(d) for d in D]
+    K = [torch.zeros_like(d) for d in D]
+    bt = Batch(bases, D, J, K, tau=1e-10)
+    # FP64: summation order only; mixed: the batch and the single build split the
+    # bra primitive pairs differently, so FP32 partial sums round differently
+    for prec, tol in [(FSIM_FP64, 1e-11), (FSIM_MIXED, 2e-6)]:
+        for rep in range(2):  # second pass replays the graph
+            for x in J + K:
+                x.fill_(np.nan)
+            bt.fock(prec, use_graph=use_graph)
+            torch.cuda.synchronize()
+            for b, d, j, k in zip(bases, D, J, K):
+                jr, kr = b.fock_build(d, tau=1e-10, precision=prec)
+                torch.cuda.synchronize()
+                s = max(1.0, torch.abs(jr).max().item())
+                assert torch.abs(j - jr).max().item() < tol * s and torch.abs(k - kr).max().item() < tol * s
+
+
+def test_batch_active_flags_skip_molecules():
+    from paper_2510_24968_gb300 import FSIM_MIXED, Basis, Batch
+    mols = _mols()[:4]
+    bases = [Basis(m) for m in mols]
+    D = [torch.eye(b.nbf, dtype=torch.float64, device="cuda") for b in bases]
+    J = [torch.zeros_like(d) for d in D]
+    K = [torch.zeros_like(d) for d in D]
+    bt = Batch(bases, D, J, K)
+    for x in J + K:
+        x.fill_(7.0)
+    bt.fock(FSIM_MIXED, active=[1, 0, 1, 0], use_graph=True)
+    torch.cuda.synchronize()
+    assert torch.all(J[1] == 7.0) and torch.all(K[3] == 7.0)
+    assert not torch.all(J[0] == 7.0) and not torch.all(K[2] == 7.0)
+
+
+def test_scf_batched_matches_single_and_oracle():
+    from oracle import OracleBasis, rhf
+    from paper_2510_24968_gb300 import FSIM_FP64, FSIM_MIXED, Basis, scf_batched
+    mols = [workload("water"), water_cluster(2, geom_seed=7), water_cluster(3, geom_seed=9),
+            water_cluster(4, geom_seed=5)]
+    bases = [Basis(m) for m in mols]
+    res64 = scf_batched(bases, precision=FSIM_FP64, tau=1e-10)
+    resmx = scf_batched(bases, precision=FSIM_MIXED, tau=1e-10)
+    for m, b, r64, rmx in zip(mols, bases, res64, resmx):
+        single = b.scf(precision=FSIM_FP64, tau=1e-10)
+        assert r64["converged"] and rmx["converged"]
+        assert abs(r64["e_total"] - single["e_total"]) < 1e-8
+        assert abs(rmx["e_total"] - single["e_total"]) < 1e-8
+        # FP64 lockstep follows the single-molecule iteration exactly
+        n = min(len(single["energies"]), len(r64["energies"]))
+        assert np.abs(r64["energies"][:n] - single["energies"][:n]).max() < 1e-9
+    ob = OracleBasis(mols[0])
+    S, H = ob.onee("S"), ob.onee("T") + ob.onee("V")
+    ro = rhf(S, H, lambda D: ob.jk(D, tau=1e-10)[:2], mols[0].nelec, ob.enuc())
+    assert abs(res64[0]["e_total"] - ro.e_total) < 1e-8
+
+
+def test_scf_batched_uneven_set():
+    # molecules of the batched workload generator (uneven heavy-atom counts): the
+    # lockstep iteration must follow each molecule's own single-molecule SCF
+    from paper_2510_24968_gb300 import FSIM_FP64, Basis, scf_batched
+    mols = [m for m in batched_set(6, seed=3, nmin=3, nmax=5)]
+    bases = [Basis(m) for m in mols]
+    res = scf_batched(bases, precision=FSIM_FP64, tau=1e-11, max_iter=12)
+    for b, r in zip(bases, res):
+        single = b.scf(precision=FSIM_FP64, tau=1e-11, max_iter=12)
+        n = min(len(single["energies"]), len(r["energies"]), 12)
+        assert n >= 5
+        assert np.abs(r["energies"][:n] - single["energies"][:n]).max() < 1e-8
+
+
+def test_autotune_keeps_results():
+    from paper_2510_24968_gb300 import FSIM_MIXED, Basis
+    b = Basis(workload("water8"))
+    d = np.random.default_rng(1).standard_normal((b.nbf, b.nbf)) * 0.05
+    D = torch.from_numpy(d + d.T).cuda()
+    J0, K0 = b.fock_build(D, tau=1e-10, precision=FSIM_MIXED)
+    choice = b.autotune(tau=1e-10, precision=FSIM_MIXED)
+    assert choice and all(c in (-2, -1, 1, 3, 9) for c, _ in choice.values())
+    J1, K1 = b.fock_build(D, tau=1e-10, precision=FSIM_MIXED)
+    torch.cuda.synchronize()
+    s = torch.abs(J0).max().item()
+    assert torch.abs(J1 - J0).max().item() < 1e-6 * s and torch.abs(K1 - K0).max().item() < 1e-6 * s
