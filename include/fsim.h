@@ -44,7 +44,7 @@ extern "C" {
 #define FSIM_PTR_DEVICE 1
 
 #define FSIM_GUESS_CORE 0     /* diagonalise H_core in the orthogonal basis (Sec. 3.2, step 1) */
-#define FSIM_GUESS_DENSITY 1  /* caller-supplied density fsim_scf_opts.D0 */
+#define FSIM_GUESS_DENSITY 1  /* caller-supplied density fsim_scf_opts.D0 (checked; core-H fallback) */
 
 typedef struct fsim_basis fsim_basis; /* opaque, owned by the library */
 
@@ -260,6 +260,44 @@ void fsim_batch_destroy(fsim_batch* batch);
  * time_s is the time at which that molecule converged.
  */
 int fsim_scf_batched(fsim_basis* const* bases, int nmol, const fsim_scf_opts* opts, fsim_scf_result* results);
+
+/*
+ * Learned initial density (a network that predicts the SCF starting density
+ * from geometry; the converged SCF is unchanged, only the number of iterations).
+ * Per atom pair (A <= B, row-major over A then B; npairs = natom (natom+1)/2):
+ * fsim_guess_features writes 48 rotation-invariant features (host, npairs x 48);
+ * fsim_guess_targets turns a density D (host, nbf^2) into the pair blocks in
+ * pair-local frames (host, npairs x 225, row-major 15 x 15, zero padded) and
+ * their mask; fsim_guess_assemble rotates predicted local blocks (device,
+ * npairs x 225 FP32) back and writes the full density (device, nbf^2 FP64).
+ * Atoms must own contiguous shells with at most 15 functions.
+ */
+int fsim_guess_layout(const fsim_basis* b, int* npairs, int* nfeat, int* nout);
+int fsim_guess_features(const fsim_basis* b, float* feat);
+int fsim_guess_targets(const fsim_basis* b, const double* D, float* target, float* mask);
+int fsim_guess_assemble(fsim_basis* b, const float* blocks, double* D, void* stream);
+
+/*
+ * The network: three linear layers with SiLU (nin -> width -> width -> nout),
+ * FP32 master weights with BF16 copies; forward and backward GEMMs on the
+ * tensor cores (BF16 inputs, FP32 accumulation), Adam (beta 0.9/0.999, eps
+ * 1e-8).  init_params: host array of fsim_mlp_nparams() floats laid out
+ * W1 [nin x width], b1, W2 [width x width], b2, W3 [width x nout], b3 (row-major).
+ * x, y, t, mask: device FP32 arrays (batch x nin / batch x nout).  loss =
+ * sum(mask (y - t)^2) / sum(mask).  fsim_mlp_grad returns that loss and its
+ * gradient (host, nparams floats; bf16 = 0 computes every product in FP32, for
+ * gradient checks); fsim_mlp_params copies parameters out (host_out) and/or in.
+ */
+typedef struct fsim_mlp fsim_mlp;
+int fsim_mlp_create(int nin, int width, int nout, const float* init_params, fsim_mlp** out);
+void fsim_mlp_destroy(fsim_mlp* net);
+long long fsim_mlp_nparams(const fsim_mlp* net);
+int fsim_mlp_params(fsim_mlp* net, float* host_out, const float* host_in);
+int fsim_mlp_forward(fsim_mlp* net, const float* x, float* y, int batch, int bf16, void* stream);
+int fsim_mlp_grad(fsim_mlp* net, const float* x, const float* t, const float* mask, int batch, int bf16, float* loss,
+                  float* grad_host, void* stream);
+int fsim_mlp_train_step(fsim_mlp* net, const float* x, const float* t, const float* mask, int batch, float lr,
+                        float* loss, void* stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* fsim_last_error(void);

@@ -258,6 +258,7 @@ int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res) {
   FSIM_TRY(mem.alloc(&eg.work, eg.lwork));
   const int th = 256, bl = (int)std::min<size_t>((n2 + th - 1) / th, 1024);
   dim3 g2((N + 127) / 128, N);
+  int rc = FSIM_OK;
 
   // one-electron matrices and H = T + V
   FSIM_TRY(onee_device(b, 0, S, c.s));
@@ -293,12 +294,36 @@ int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res) {
     BLAS_CK(cublasDgemm(c.blas, CUBLAS_OP_N, CUBLAS_OP_T, N, N, nocc, &two, tmp, N, tmp, N, &zero, Dout, N));
     return FSIM_OK;
   };
+  res->guess_fallback = 0;
   if (o.guess == FSIM_GUESS_DENSITY) {
-    FSIM_CK(cudaMemcpyAsync(D, o.D0, sizeof(double) * n2, cudaMemcpyHostToDevice, c.s));
+    // supplied guess (e.g. the learned one): symmetrise, rescale to Tr(DS) = N_e,
+    // and keep it only if |Tr(DS) - N_e| <= 0.5 before rescaling and
+    // ||D S D - 2 D||_F / ||D||_F <= 0.2 after; otherwise fall back to core-H
+    FSIM_CK(cudaMemcpyAsync(tmp, o.D0, sizeof(double) * n2, cudaMemcpyHostToDevice, c.s));
+    antisym_kernel<<<g2, 128, 0, c.s>>>(tmp, e, N);           // e = D0 - D0^T
+    add_kernel<<<bl, th, 0, c.s>>>(tmp, e, -0.5, D, n2);       // D = (D0 + D0^T) / 2
+    const double tr = host_dot(c, scratch, D, S, n2, 0, &rc);
+    if (rc != FSIM_OK) return rc;
+    bool ok = std::fabs(tr - o.nelec) <= 0.5 && tr > 0.0;
+    if (ok) {
+      const double f = o.nelec / tr;
+      add_kernel<<<bl, th, 0, c.s>>>(D, D, f - 1.0, D, n2);
+      FSIM_TRY(gemm_rm(c, false, false, N, N, N, D, N, S, N, tmp, N));    // D S
+      FSIM_TRY(gemm_rm(c, false, false, N, N, N, tmp, N, D, N, tmp2, N));  // D S D
+      add_kernel<<<bl, th, 0, c.s>>>(tmp2, D, -2.0, tmp2, n2);
+      const double num = host_dot(c, scratch, tmp2, tmp2, n2, 0, &rc);
+      if (rc != FSIM_OK) return rc;
+      const double den = host_dot(c, scratch, D, D, n2, 0, &rc);
+      if (rc != FSIM_OK) return rc;
+      ok = std::sqrt(num / den) <= 0.2;
+    }
+    if (!ok) {
+      res->guess_fallback = 1;
+      FSIM_TRY(density_from(H, D));
+    }
   } else {
     FSIM_TRY(density_from(H, D));
   }
-  res->guess_fallback = 0;
   res->e_nuc = 0.0;
   FSIM_TRY(fsim_enuc(b, &res->e_nuc));
 
@@ -320,7 +345,6 @@ int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res) {
   res->fp64_builds = 0;
   res->mixed_builds = 0;
   int it = 0;
-  int rc = FSIM_OK;
   const double t_loop0 = elapsed();
   for (it = 1; it <= o.max_iter; ++it) {
     // ---- G(D), full or incremental

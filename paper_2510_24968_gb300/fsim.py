@@ -34,7 +34,9 @@ EXPORTS = ["fsim_basis_create", "fsim_basis_destroy", "fsim_basis_nbf", "fsim_ba
            "fsim_basis_pair_counts", "fsim_enuc", "fsim_onee", "fsim_schwarz", "fsim_fock_opts_default",
            "fsim_fock_build", "fsim_fock_build_noalloc", "fsim_autotune", "fsim_last_quartet_count", "fsim_last_class_times", "fsim_eri_quartets", "fsim_eri_dump",
            "fsim_scf_opts_default", "fsim_scf", "fsim_batch_create", "fsim_batch_fock", "fsim_batch_destroy",
-           "fsim_scf_batched", "fsim_last_error"]
+           "fsim_scf_batched", "fsim_guess_layout", "fsim_guess_features", "fsim_guess_targets",
+           "fsim_guess_assemble", "fsim_mlp_create", "fsim_mlp_destroy", "fsim_mlp_nparams", "fsim_mlp_params",
+           "fsim_mlp_forward", "fsim_mlp_grad", "fsim_mlp_train_step", "fsim_last_error"]
 
 
 class FsimError(RuntimeError):
@@ -113,6 +115,20 @@ def load():
     L.fsim_batch_destroy.argtypes = [vp]
     L.fsim_batch_destroy.restype = None
     L.fsim_scf_batched.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(fsim_scf_opts), C.POINTER(fsim_scf_result)]
+    fp = C.POINTER(C.c_float)
+    L.fsim_guess_layout.argtypes = [vp, ip, ip, ip]
+    L.fsim_guess_features.argtypes = [vp, fp]
+    L.fsim_guess_targets.argtypes = [vp, dp, fp, fp]
+    L.fsim_guess_assemble.argtypes = [vp, vp, vp, vp]
+    L.fsim_mlp_create.argtypes = [C.c_int, C.c_int, C.c_int, fp, C.POINTER(vp)]
+    L.fsim_mlp_destroy.argtypes = [vp]
+    L.fsim_mlp_destroy.restype = None
+    L.fsim_mlp_nparams.argtypes = [vp]
+    L.fsim_mlp_nparams.restype = C.c_longlong
+    L.fsim_mlp_params.argtypes = [vp, fp, fp]
+    L.fsim_mlp_forward.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp]
+    L.fsim_mlp_grad.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int, fp, fp, vp]
+    L.fsim_mlp_train_step.argtypes = [vp, vp, vp, vp, C.c_int, C.c_float, fp, vp]
     L.fsim_last_error.restype = C.c_char_p
     _lib = L
     return L

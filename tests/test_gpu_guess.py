@@ -1,0 +1,116 @@
+"""Learned initial density: network kernels against the FP64 oracle network,
+pair-local frames against rotation covariance, the guess check/fallback, and a
+small end-to-end gain (fewer SCF iterations, same energy)."""
+import math
+
+import numpy as np
+import pytest
+
+from fsim_synth import water_cluster
+
+from .helpers import make_mol
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_24968_gb300.build import build
+    build()
+
+
+def _net_and_data(width=32, b=300, seed=0):
+    from paper_2510_24968_gb300.guess import GuessNet
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal((b, 48)).astype(np.float32)
+    t = rng.standard_normal((b, 225)).astype(np.float32) * 0.3
+    m = (rng.random((b, 225)) > 0.5).astype(np.float32)
+    net = GuessNet(width=width, seed=5)
+    return net, x, t, m
+
+
+def test_mlp_forward_and_gradient_match_fp64_oracle():
+    from oracle import mlp
+    net, x, t, m = _net_and_data()
+    p = net.params().astype(np.float64)
+    xd, td, md = (torch.from_numpy(a).cuda() for a in (x, t, m))
+    y = torch.empty((x.shape[0], 225), dtype=torch.float32, device="cuda")
+    yo, _ = mlp.forward(p, x.astype(np.float64), 48, 32, 225)
+    net.forward(xd.data_ptr(), y.data_ptr(), x.shape[0], bf16=False)
+    torch.cuda.synchronize()
+    assert np.abs(y.cpu().numpy() - yo).max() < 1e-5 * max(1.0, np.abs(yo).max())
+    net.forward(xd.data_ptr(), y.data_ptr(), x.shape[0], bf16=True)
+    torch.cuda.synchronize()
+    assert np.abs(y.cpu().numpy() - yo).max() < 3e-2 * max(1.0, np.abs(yo).max())
+    loss, g = net.grad(xd.data_ptr(), td.data_ptr(), md.data_ptr(), x.shape[0], bf16=False)
+    go = mlp.grad(p, x.astype(np.float64), t.astype(np.float64), m.astype(np.float64), 48, 32, 225)
+    assert loss == pytest.approx(mlp.loss(p, x, t, m, 48, 32, 225), rel=1e-5)
+    assert np.linalg.norm(g - go) / np.linalg.norm(go) < 1e-4
+    _, gb = net.grad(xd.data_ptr(), td.data_ptr(), md.data_ptr(), x.shape[0], bf16=True)
+    assert np.linalg.norm(gb - go) / np.linalg.norm(go) < 5e-2
+
+
+def test_training_reduces_loss():
+    from paper_2510_24968_gb300.guess import train
+    net, x, t, m = _net_and_data(width=64, b=512, seed=1)
+    losses = train(net, x, t * 0 + np.tanh(x[:, :1]) * 0.5, m, steps=200, batch=256, lr0=3e-3, log_every=50)
+    assert losses[-1][1] < 0.25 * losses[0][1]
+
+
+def _rotated(mol, th=0.9):
+    Rm = np.array([[math.cos(th), -math.sin(th), 0.0], [math.sin(th), math.cos(th), 0.0], [0.0, 0.0, 1.0]])
+    Rm = Rm @ np.array([[1, 0, 0], [0, math.cos(0.4), -math.sin(0.4)], [0, math.sin(0.4), math.cos(0.4)]])
+    return make_mol([(z, tuple(Rm @ x + np.array([0.3, -1.1, 2.0]))) for z, x in zip(mol.Z, mol.xyz)],
+                    [(s.atom, s.l, s.alpha, s.coef) for s in mol.shells])
+
+
+def test_local_blocks_rotation_invariant_and_round_trip():
+    from paper_2510_24968_gb300 import FSIM_FP64, Basis
+    from paper_2510_24968_gb300.guess import features, load, targets, _check
+    import ctypes as C
+    mol = water_cluster(2, geom_seed=21)
+    b1, b2 = Basis(mol), Basis(_rotated(mol))
+    r1 = b1.scf(precision=FSIM_FP64, tau=1e-12, want_density=True)
+    r2 = b2.scf(precision=FSIM_FP64, tau=1e-12, want_density=True)
+    assert abs(r1["e_total"] - r2["e_total"]) < 1e-9
+    assert np.abs(features(b1) - features(b2)).max() < 1e-5
+    t1, m1 = targets(b1, r1["D"])
+    t2, m2 = targets(b2, r2["D"])
+    assert np.array_equal(m1, m2)
+    assert np.abs(t1 - t2).max() < 1e-5
+    # assembling the exact local blocks gives back the density
+    y = torch.from_numpy(t1).cuda()
+    D = torch.zeros((b1.nbf, b1.nbf), dtype=torch.float64, device="cuda")
+    _check(load().fsim_guess_assemble(b1.h, C.c_void_p(y.data_ptr()), C.c_void_p(D.data_ptr()), None))
+    assert np.abs(D.cpu().numpy() - r1["D"]).max() < 1e-5 * max(1.0, np.abs(r1["D"]).max())
+
+
+def test_bad_guess_falls_back_to_core():
+    from paper_2510_24968_gb300 import FSIM_FP64, Basis
+    b = Basis(water_cluster(2, geom_seed=3))
+    core = b.scf(precision=FSIM_FP64, tau=1e-10)
+    bad = b.scf(precision=FSIM_FP64, tau=1e-10, D0=np.zeros((b.nbf, b.nbf)))
+    assert bad["guess_fallback"] and bad["iters"] == core["iters"]
+    assert abs(bad["e_total"] - core["e_total"]) < 1e-10
+
+
+def test_learned_guess_saves_iterations_small():
+    from paper_2510_24968_gb300 import FSIM_MIXED, Basis
+    from paper_2510_24968_gb300.guess import GuessNet, predict_density, train, training_data
+    train_mols = [water_cluster(k, geom_seed=10**6 + i) for i, k in enumerate([2, 3] * 12)]
+    X, T, M, _ = training_data(train_mols)
+    net = GuessNet(seed=3)
+    train(net, X, T, M, steps=400, batch=2048, lr0=1e-3)
+    gain = []
+    for i in range(2):
+        b = Basis(water_cluster(4, geom_seed=2 * 10**6 + i))
+        core = b.scf(precision=FSIM_MIXED, tau=1e-10)
+        learned = b.scf(precision=FSIM_MIXED, tau=1e-10, D0=predict_density(b, net))
+        assert core["converged"] and learned["converged"] and not learned["guess_fallback"]
+        assert abs(learned["e_total"] - core["e_total"]) < 1e-8
+        gain.append(core["iters"] - learned["iters"])
+    assert sum(gain) > 0

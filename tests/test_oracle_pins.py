@@ -457,3 +457,21 @@ def test_scf_rotation_invariance(water_scf):
     S2, H2 = B2.onee("S"), B2.onee("T") + B2.onee("V")
     r2 = rhf(S2, H2, lambda D: B2.jk(D)[:2], m.nelec, B2.enuc())
     assert r2.e_total == pytest.approx(r.e_total, abs=1e-9)
+
+
+# ---------------------------------------------------------------- learned-guess network (FP64 reference)
+def test_mlp_oracle_gradient_finite_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(0)
+    nin, w, nout, b = 5, 7, 4, 6
+    p = rng.standard_normal(mlp.nparams(nin, w, nout)) * 0.5
+    x = rng.standard_normal((b, nin))
+    t = rng.standard_normal((b, nout))
+    mask = (rng.random((b, nout)) > 0.3).astype(float)
+    g = mlp.grad(p, x, t, mask, nin, w, nout)
+    h = 1e-6
+    for i in rng.choice(len(p), 25, replace=False):
+        e = np.zeros_like(p)
+        e[i] = h
+        fd = (mlp.loss(p + e, x, t, mask, nin, w, nout) - mlp.loss(p - e, x, t, mask, nin, w, nout)) / (2 * h)
+        assert g[i] == pytest.approx(fd, rel=1e-6, abs=1e-9)
