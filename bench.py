@@ -198,6 +198,7 @@ def run_ours(args):
 
     gb = Basis(mol)
     gb.schwarz()
+    tuned = gb.autotune(tau=args.tau, precision=FSIM_MIXED, shard=rank, nshards=world) if not args.no_tune else {}
     N = gb.nbf
     Dn = np.random.default_rng(0).standard_normal((N, N)) * 0.05
     Dn = Dn + Dn.T
@@ -322,6 +323,7 @@ def run_ours(args):
                            "fp64_achieved": all_fl / (ms_fp64 * 1e-3) / 1e12,
                            "frac_fp64": all_fl / (ms_fp64 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS},
         "class_ms": {f"{names[k[0]]}|{names[k[1]]}": round(tot[k] / len(cls_mixed[k]), 4) for k in tot},
+        "autotune": {f"{names[k[0]]}|{names[k[1]]}": v[0] for k, v in tuned.items()},
         "cpu_baseline": cpu,
         "e2e": {"value": q_mixed / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * N * 8,
                 "d2h_bytes_per_step": 2 * N * N * 8},
@@ -342,6 +344,7 @@ def main():
     ap.add_argument("--tau", type=float, default=1e-10)
     ap.add_argument("--no-scf", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -101,10 +101,10 @@ def test_bad_guess_falls_back_to_core():
 def test_learned_guess_saves_iterations_small():
     from paper_2510_24968_gb300 import FSIM_MIXED, Basis
     from paper_2510_24968_gb300.guess import GuessNet, predict_density, train, training_data
-    train_mols = [water_cluster(k, geom_seed=10**6 + i) for i, k in enumerate([2, 3] * 12)]
+    train_mols = [water_cluster(k, geom_seed=10**6 + i) for i, k in enumerate([2, 3, 4] * 20)]
     X, T, M, _ = training_data(train_mols)
     net = GuessNet(seed=3)
-    train(net, X, T, M, steps=400, batch=2048, lr0=1e-3)
+    train(net, X, T, M, steps=1500, batch=2048, lr0=1e-3)
     gain = []
     for i in range(2):
         b = Basis(water_cluster(4, geom_seed=2 * 10**6 + i))
