@@ -114,6 +114,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def allreduce_sum(tensors):
+    """Sum partial J/K (or counts) over the ranks in place (the exchange step of
+    a sharded Fock build); no-op on one rank."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        for t in tensors:
+            dist.all_reduce(t)
+    return tensors
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """Largest value over the ranks (timings are reported as the slowest rank)."""
+    import torch
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        t = torch.tensor([value], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return value
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -212,8 +233,7 @@ def run_ours(args):
         gb.fock_build(D, J, K, tau=args.tau, precision=prec, stream=sptr, shard=rank, nshards=world,
                       timing=timing)
         if world > 1:
-            torch.distributed.all_reduce(J)
-            torch.distributed.all_reduce(K)
+            allreduce_sum([J, K])
 
     def timed(prec, steps, warmup):
         for _ in range(warmup):
@@ -238,13 +258,10 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
-        ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+        ms = max_over_ranks(sum(e0.elapsed_time(e1) for e0, e1 in ev), dev)
         if world > 1:
-            tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            ms = float(tt.item())
             qq = torch.tensor([quartets], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(qq)
+            allreduce_sum([qq])
             quartets = int(qq.item())
         return ms / steps, quartets, per_class, launches, q
 
@@ -274,11 +291,7 @@ def run_ours(args):
     ne = max(3, args.steps)
     for _ in range(ne):
         gb.fock_build(Dnp, Jnp, Knp, tau=args.tau, precision=FSIM_MIXED, stream=sptr, shard=rank, nshards=world)
-    e2e_s = (time.perf_counter() - t0) / ne
-    if world > 1:
-        tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / ne, dev)
 
     # time to a converged energy, mixed vs FP64 (rank 0, whole molecule on one GPU)
     tte = None

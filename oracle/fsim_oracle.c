@@ -462,18 +462,25 @@ void orc_schwarz(const void *vB, double *Q) {
  * when Q_ab Q_cd < tau (tau <= 0: no screening).  OpenMP over bra pairs
  * with per-thread J/K, summed at the end.
  */
-void orc_jk_sample(const void *vB, const double *D, double *J, double *K, double tau, int nthreads,
-                   long long *n_quartets, int bra_stride);
+void orc_jk_shard(const void *vB, const double *D, double *J, double *K, double tau, int nthreads,
+                  long long *n_quartets, int shard, int nshards);
 
 void orc_jk(const void *vB, const double *D, double *J, double *K, double tau, int nthreads,
             long long *n_quartets) {
-    orc_jk_sample(vB, D, J, K, tau, nthreads, n_quartets, 1);
+    orc_jk_shard(vB, D, J, K, tau, nthreads, n_quartets, 0, 1);
 }
 
 /* As orc_jk, restricted to the bra pairs ij with ij % bra_stride == 0: a
  * bounded sample of the same work, for timing the oracle on large cases. */
 void orc_jk_sample(const void *vB, const double *D, double *J, double *K, double tau, int nthreads,
                    long long *n_quartets, int bra_stride) {
+    orc_jk_shard(vB, D, J, K, tau, nthreads, n_quartets, 0, bra_stride);
+}
+
+/* The contribution of the bra pairs ij with ij % nshards == shard; the sum
+ * over all shards is orc_jk. */
+void orc_jk_shard(const void *vB, const double *D, double *J, double *K, double tau, int nthreads,
+                  long long *n_quartets, int shard, int nshards) {
     const orc_basis *B = (const orc_basis *)vB;
     int N = B->nbf, ns = B->nshell;
     double *Q = NULL;
@@ -498,7 +505,7 @@ void orc_jk_sample(const void *vB, const double *D, double *J, double *K, double
         double blk[ORC_NCMAX * ORC_NCMAX * ORC_NCMAX * ORC_NCMAX];
 #pragma omp for schedule(dynamic, 1)
         for (int ij = 0; ij < npair; ++ij) {
-            if (ij % bra_stride) continue;
+            if (ij % nshards != shard) continue;
             for (int kl = 0; kl <= ij; ++kl) {
                 int s[4] = {pa[ij], pb[ij], pa[kl], pb[kl]};
                 if (Q && Q[s[0] * ns + s[1]] * Q[s[2] * ns + s[3]] < tau) continue;

@@ -57,6 +57,8 @@ def lib():
                                  C.POINTER(C.c_longlong)]
             L.orc_jk_sample.argtypes = [C.c_void_p, _dp, _dp, _dp, C.c_double, C.c_int,
                                         C.POINTER(C.c_longlong), C.c_int]
+            L.orc_jk_shard.argtypes = [C.c_void_p, _dp, _dp, _dp, C.c_double, C.c_int,
+                                       C.POINTER(C.c_longlong), C.c_int, C.c_int]
             L.orc_jk_block.argtypes = [C.c_void_p, _dp, C.c_int, C.c_int, _dp, _dp, C.c_double, _dp]
             L.orc_jacobi_eigh.restype = C.c_int
             L.orc_jacobi_eigh.argtypes = [C.c_int, _dp, _dp, _dp]
@@ -164,6 +166,16 @@ class OracleBasis:
         K = np.zeros((N, N))
         nq = C.c_longlong(0)
         lib().orc_jk_sample(self.h, D, J, K, float(tau), int(nthreads), C.byref(nq), int(bra_stride))
+        return J, K, nq.value
+
+    def jk_shard(self, D: np.ndarray, shard: int, nshards: int, tau: float = 0.0, nthreads: int = 0):
+        """J/K contributions of the bra pairs ij with ij % nshards == shard."""
+        N = self.nbf
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        J = np.zeros((N, N))
+        K = np.zeros((N, N))
+        nq = C.c_longlong(0)
+        lib().orc_jk_shard(self.h, D, J, K, float(tau), int(nthreads), C.byref(nq), int(shard), int(nshards))
         return J, K, nq.value
 
     def jk(self, D: np.ndarray, tau: float = 0.0, nthreads: int = 0):
