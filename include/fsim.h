@@ -152,14 +152,14 @@ int fsim_fock_build_noalloc(fsim_basis* b, const double* D, double* J, double* K
  * Autotuner for the Fock-build launches of this basis and these options
  * (screening, precision, shard): for every class pair it times each launch
  * shape on the device -- the unrolled per-class kernel with the bra primitive
- * pairs split over 1, 3 or 9 threads (tiles of 128, 42 or 14 kets per CTA),
- * in mixed precision also its chunk-warp form (one warp per ket-component
- * chunk, tiles of 32 kets), and the warp-cooperative kernel (4 kets per CTA)
- * -- and keeps the fastest in the basis' cached plan, which later
+ * pairs split over psplit = 1, 3 or 9 threads and the ket-component chunks
+ * shared out over csplit = 1, 2 or 4 warp groups (a CTA of 128 threads takes
+ * 128 / csplit / psplit kets), and the warp-cooperative kernel (4 kets per
+ * CTA) -- and keeps the fastest in the basis' cached plan, which later
  * fsim_fock_build calls with the same options use.  choice (36 entries,
- * optional): chosen split, -2 chunk-warp, -1 cooperative kernel, 0 for class
- * pairs without work; best_ms (36, optional):
- * its median time.  Index X*6+Y as in fsim_last_class_times.
+ * optional): 10 * psplit + csplit for the unrolled kernel, -1 for the
+ * cooperative kernel, 0 for class pairs without work; best_ms (36,
+ * optional): its median time.  Index X*6+Y as in fsim_last_class_times.
  */
 int fsim_autotune(fsim_basis* b, const fsim_fock_opts* opts, int* choice, float* best_ms);
 

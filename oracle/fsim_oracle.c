@@ -431,6 +431,15 @@ void orc_eri_full(const void *vB, double *g) {
     }
 }
 
+/* A list of nq shell quartets q[4*i .. 4*i+3]; block i is written at
+ * out + off[i] in the layout of orc_eri_shell_quartet.  Each quartet is
+ * independent, so the list is shared out over OpenMP threads. */
+void orc_eri_quartet_list(const void *vB, int nq, const int *q, const long long *off, double *out) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int i = 0; i < nq; ++i)
+        orc_eri_shell_quartet(vB, q[4 * i], q[4 * i + 1], q[4 * i + 2], q[4 * i + 3], out + off[i]);
+}
+
 /* Shell-level Schwarz bounds Q[a*nshell+b] = sqrt(max |(mu nu|mu nu)|). */
 void orc_schwarz(const void *vB, double *Q) {
     const orc_basis *B = (const orc_basis *)vB;

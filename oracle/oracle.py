@@ -52,6 +52,7 @@ def lib():
             L.orc_enuc.argtypes = [C.c_void_p]
             L.orc_eri_shell_quartet.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, _dp]
             L.orc_eri_full.argtypes = [C.c_void_p, _dp]
+            L.orc_eri_quartet_list.argtypes = [C.c_void_p, C.c_int, _ip, C.POINTER(C.c_longlong), _dp]
             L.orc_schwarz.argtypes = [C.c_void_p, _dp]
             L.orc_jk.argtypes = [C.c_void_p, _dp, _dp, _dp, C.c_double, C.c_int,
                                  C.POINTER(C.c_longlong)]
@@ -132,6 +133,16 @@ class OracleBasis:
         out = np.zeros(int(np.prod(n)))
         lib().orc_eri_shell_quartet(self.h, int(a), int(b), int(c), int(d), out)
         return out.reshape(n)
+
+    def eri_blocks(self, quartets) -> list:
+        """Blocks of a list of shell quartets (same layout as eri_block), OpenMP over the list."""
+        q = np.ascontiguousarray(np.asarray(quartets, dtype=np.int32).reshape(-1, 4))
+        nc = (np.asarray(self.shell_l)[q] + 1) * (np.asarray(self.shell_l)[q] + 2) // 2
+        sizes = np.prod(nc, axis=1).astype(np.int64)
+        off = np.ascontiguousarray(np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64))
+        out = np.zeros(int(sizes.sum()))
+        lib().orc_eri_quartet_list(self.h, len(q), q, off.ctypes.data_as(C.POINTER(C.c_longlong)), out)
+        return [out[o:o + n].reshape(tuple(c)) for o, n, c in zip(off, sizes, nc)]
 
     def eri_full(self) -> np.ndarray:
         N = self.nbf

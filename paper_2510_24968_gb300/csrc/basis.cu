@@ -474,6 +474,13 @@ void fsim_basis_destroy(fsim_basis* b) {
   if (b->ev_ok)
     for (auto& pr : b->ev)
       for (auto& e : pr) cudaEventDestroy(e);
+  if (b->aux_ok) {
+    for (int k = 0; k < fsim_basis::kAuxStreams; ++k) {
+      cudaStreamDestroy(b->aux[k]);
+      cudaEventDestroy(b->join_ev[k]);
+    }
+    cudaEventDestroy(b->fork_ev);
+  }
   delete b;
 }
 

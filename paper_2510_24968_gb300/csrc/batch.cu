@@ -218,6 +218,7 @@ int launch_batch(fsim_batch* bt, int prec, cudaStream_t s) {
         p.nitems = C.nitems;
         p.same = X == Y ? 1 : 0;
         p.psplit = 1;
+        p.csplit = 1;
         p.bra_ppmax = C.bra_ppmax;
         p.boys = std::is_same<Real, double>::value ? (const Real*)bt->b[0]->d_boys64 : (const Real*)bt->b[0]->d_boys32;
         p.boys64_T = INFINITY;

@@ -74,6 +74,7 @@ struct JKParams {
   int nitems;                           // total work items
   int same;                             // bra class == ket class
   int psplit;                           // bra primitive pairs split over this many threads
+  int csplit;                           // ket chunks shared out over this many thread groups (1, 2, 4)
   int bra_ppmax;                        // largest bra primitive-pair count (shared-memory size)
   const Real* __restrict__ boys;
   float boys64_T;                       // FP32 path: Boys in FP64 at T >= this (infinity = never)
@@ -125,12 +126,13 @@ __device__ __forceinline__ double rsqrt_r<double>(double x) { return rsqrt(x); }
 template <>
 __device__ __forceinline__ float rsqrt_r<float>(float x) { return rsqrtf(x); }
 
-// Chunk bookkeeping for the ket side.
+// Chunk bookkeeping for the ket side: chunks of CS consecutive components, the
+// last one possibly shorter.
 template <class KC, int CS>
 struct KetChunks {
-  static constexpr int NCH = KC::NC / CS;
-  static_assert(KC::NC % CS == 0, "chunk must divide the ket component count");
-  __host__ __device__ static constexpr int nnz_of(int ch) { return KC::off((ch + 1) * CS) - KC::off(ch * CS); }
+  static constexpr int NCH = (KC::NC + CS - 1) / CS;
+  __host__ __device__ static constexpr int end(int ch) { return (ch + 1) * CS < KC::NC ? (ch + 1) * CS : KC::NC; }
+  __host__ __device__ static constexpr int nnz_of(int ch) { return KC::off(end(ch)) - KC::off(ch * CS); }
   __host__ __device__ static constexpr int max_nnz() {
     int m = 0;
     for (int ch = 0; ch < NCH; ++ch) m = nnz_of(ch) > m ? nnz_of(ch) : m;
@@ -138,26 +140,28 @@ struct KetChunks {
   }
 };
 
-// Contracted quartet block for one ket chunk: out[a][cs] for all bra components a
-// and ket components c = CH*CS + cs.  Bra data: accessor bra(field, pp).
-template <typename Real, int LA, int LB, int LC, int LD, int CS, int CH, class BraAt>
-__device__ __forceinline__ void quartet_chunk(Real (&out)[PairCls<LA, LB>::NC][CS], const BraAt& bra, int nppb,
-                                              int b0, int bstep, const PairView<Real>& ket, int j, int nppk,
-                                              const Real* __restrict__ boysL, int bstride, float t64) {
+// Contracted quartet block for one ket chunk: out(a, cs) for all bra components
+// a and ket components c = ch*CS + cs < NC, accumulated in this thread's
+// shared-memory slots so[(a * CS + cs) * kJKThreads] (so the registers hold
+// only R, the chunk's W and its E non-zeros).  Bra data: accessor bra(field, pp).
+// The chunk index is a runtime value (uniform across the warp), so the Boys
+// function, the R recursion, the bra transform and the caller's digestion exist
+// once in the code; only the ket transform (and its loads of the chunk's E
+// non-zeros) is specialised per chunk behind a warp-uniform branch, which keeps
+// the instruction footprint of a chunk small enough for the instruction cache.
+template <typename Real, int LA, int LB, int LC, int LD, int CS, class BraAt>
+__device__ __forceinline__ void quartet_chunk(Real* __restrict__ so, const BraAt& bra, int nppb, int b0, int bstep,
+                                              const PairView<Real>& ket, int j, int nppk,
+                                              const Real* __restrict__ boysL, int bstride, float t64, int ch) {
   using BC = PairCls<LA, LB>;
   using KC = PairCls<LC, LD>;
   using KCh = KetChunks<KC, CS>;
   constexpr int L = LA + LB + LC + LD;
   constexpr int NH = nherm(L);
   constexpr int NH1 = BC::NH;
-  constexpr int c0 = CH * CS;
-  constexpr int nzoff = KC::off(c0);
-  constexpr int NZ = KCh::nnz_of(CH);
+  constexpr int NZM = KCh::max_nnz();
 #pragma unroll
-  for (int a = 0; a < BC::NC; ++a)
-#pragma unroll
-    for (int cs = 0; cs < CS; ++cs) out[a][cs] = Real(0);
-
+  for (int x = 0; x < BC::NC * CS; ++x) so[x * kJKThreads] = Real(0);
   const size_t kstride = (size_t)ket.ppmax * ket.n;
   for (int b = b0; b < nppb; b += bstep) {
     const Real p = bra(0, b), Px = bra(1, b), Py = bra(2, b), Pz = bra(3, b);
@@ -166,14 +170,10 @@ __device__ __forceinline__ void quartet_chunk(Real (&out)[PairCls<LA, LB>::NC][C
     for (int h = 0; h < NH1; ++h)
 #pragma unroll
       for (int cs = 0; cs < CS; ++cs) W[h][cs] = Real(0);
-
     for (int k = 0; k < nppk; ++k) {
       const Real* kp = ket.pd + (size_t)k * ket.n + j;
       const auto q4 = ket.pq[(size_t)k * ket.n + j];
       const Real q = q4.x, Qx = q4.y, Qy = q4.z, Qz = q4.w;
-      Real Ek[NZ];
-#pragma unroll
-      for (int z = 0; z < NZ; ++z) Ek[z] = __ldg(kp + (size_t)(4 + nzoff + z) * kstride);
       const Real s = p + q;
       const Real rs = rsqrt_r<Real>(s);
       const Real al = p * q * (rs * rs);
@@ -191,33 +191,48 @@ __device__ __forceinline__ void quartet_chunk(Real (&out)[PairCls<LA, LB>::NC][C
       }
       Real R[NH];
       hermite_R<Real, L>(R, src, X, Y, Z);
-      // ket transform over the non-zeros of each ket component of this chunk
-      static_for<CS>([&](auto Cs) {
-        constexpr int cs = decltype(Cs)::value;
-        constexpr int c = c0 + cs;
-        constexpr int zb = KC::off(c) - nzoff;
-        static_for<KC::nnz(c)>([&](auto Kk) {
-          constexpr int kk = decltype(Kk)::value;
-          constexpr int tau = KC::nz_t(c, kk), nu = KC::nz_u(c, kk), phi = KC::nz_v(c, kk);
-          const Real e = ((tau + nu + phi) & 1) ? -Ek[zb + kk] : Ek[zb + kk];
-          static_for<NH1>([&](auto Hh) {
-            constexpr int h = decltype(Hh)::value;
-            constexpr int hr = hidx(herm_t(h) + tau, herm_u(h) + nu, herm_v(h) + phi);
-            W[h][cs] = fma(e, R[hr], W[h][cs]);
-          });
+      Real Ek[NZM];
+      static_for<KCh::NCH>([&](auto Ch) {
+        constexpr int CH = decltype(Ch)::value;
+        if (ch != CH) return;
+        constexpr int c0 = CH * CS;
+        constexpr int nzoff = KC::off(c0);
+        constexpr int NZ = KCh::nnz_of(CH);
+#pragma unroll
+        for (int z = 0; z < NZ; ++z) Ek[z] = __ldg(kp + (size_t)(4 + nzoff + z) * kstride);
+        static_for<CS>([&](auto Cs) {
+          constexpr int cs = decltype(Cs)::value;
+          constexpr int c = c0 + cs;
+          if constexpr (c < KC::NC) {
+            constexpr int zb = KC::off(c) - nzoff;
+            static_for<KC::nnz(c)>([&](auto Kk) {
+              constexpr int kk = decltype(Kk)::value;
+              constexpr int tau = KC::nz_t(c, kk), nu = KC::nz_u(c, kk), phi = KC::nz_v(c, kk);
+              const Real e = ((tau + nu + phi) & 1) ? -Ek[zb + kk] : Ek[zb + kk];
+              static_for<NH1>([&](auto Hh) {
+                constexpr int h = decltype(Hh)::value;
+                constexpr int hr = hidx(herm_t(h) + tau, herm_u(h) + nu, herm_v(h) + phi);
+                W[h][cs] = fma(e, R[hr], W[h][cs]);
+              });
+            });
+          }
         });
       });
     }
-    // bra transform with this bra primitive pair's E non-zeros
     static_for<BC::NC>([&](auto Aa) {
       constexpr int a = decltype(Aa)::value;
+      Real acc[CS];
+#pragma unroll
+      for (int cs = 0; cs < CS; ++cs) acc[cs] = Real(0);
       static_for<BC::nnz(a)>([&](auto Kk) {
         constexpr int kk = decltype(Kk)::value;
         constexpr int h = hidx(BC::nz_t(a, kk), BC::nz_u(a, kk), BC::nz_v(a, kk));
         const Real e = bra(4 + BC::off(a) + kk, b);
 #pragma unroll
-        for (int cs = 0; cs < CS; ++cs) out[a][cs] = fma(e, W[h][cs], out[a][cs]);
+        for (int cs = 0; cs < CS; ++cs) acc[cs] = fma(e, W[h][cs], acc[cs]);
       });
+#pragma unroll
+      for (int cs = 0; cs < CS; ++cs) so[(a * CS + cs) * kJKThreads] += acc[cs];
     });
   }
 }
@@ -233,7 +248,8 @@ __device__ __forceinline__ int find_bra(const int* __restrict__ prefix, int n, i
 }
 
 // Fused ERI + J/K kernel, persistent: each CTA walks work items (bra pair,
-// tile of kets) with a grid stride; threads = (ket, bra-primitive subset).
+// tile of kets) with a grid stride; threads = (ket chunk group, ket,
+// bra-primitive subset).
 // Shared memory: the Boys table columns L..L+K-1 (loaded once per CTA), the
 // bra block of D, the bra block of J_acc and the bra primitive data.
 // Accumulates J_acc, K_acc with the 8-fold degeneracy factor; the caller
@@ -255,13 +271,19 @@ __global__ void __launch_bounds__(kJKThreads) jk_kernel(JKParams<Real> P) {
   Real* sBoys = reinterpret_cast<Real*>(smem_raw);                     // [BR][BK]
   Real* sDab = reinterpret_cast<Real*>(smem_raw + (jk_boys_smem<Real>() + 15) / 16 * 16);  // D bra block
   Real* sJw = sDab + BC::NC;               // per-warp partials of J_acc for the bra block [warp][a]
-  Real* sbra = sJw + NWARP * BC::NC;       // bra primitive data [pp][field]
+  Real* sOut = sJw + NWARP * BC::NC;       // per-thread quartet chunk out(a, cs) [a * CS + cs][thread]
+  Real* sJb = sOut + BC::NC * CS * kJKThreads;  // per-thread part of J_acc for the bra block [a][thread]
+  Real* sbra = sJb + BC::NC * kJKThreads;  // bra primitive data [pp][field]
 
   for (int x = threadIdx.x; x < BR * BK; x += blockDim.x)
     sBoys[x] = P.boys[(x / BK) * kBoysCols + L + x % BK];
-  const int ps = P.psplit;
-  const int tq = blockDim.x / ps;
-  const int q = threadIdx.x / ps, bs = threadIdx.x % ps;
+  // thread = (chunk group cg, ket q of the tile, bra-primitive subset bs); the
+  // chunk group is the slowest index, so it is uniform within each warp
+  const int ps = P.psplit, ncg = P.csplit;
+  const int gsz = blockDim.x / ncg;
+  const int cg = threadIdx.x / gsz, t = threadIdx.x % gsz;
+  const int tq = gsz / ps;
+  const int q = t / ps, bs = t % ps;
   const int lane = threadIdx.x & 31;
 
   for (int item = blockIdx.x; item < P.nitems; item += gridDim.x) {
@@ -288,31 +310,33 @@ __global__ void __launch_bounds__(kJKThreads) jk_kernel(JKParams<Real> P) {
     __syncthreads();
 
     const int j = tile * tq + q;
-    Real jb[BC::NC];  // this thread's part of J_acc for the bra block
+    Real* so = sOut + threadIdx.x;
+    Real* jb = sJb + threadIdx.x;  // this thread's part of J_acc for the bra block, jb[a * kJKThreads]
 #pragma unroll
-    for (int a = 0; a < BC::NC; ++a) jb[a] = Real(0);
+    for (int a = 0; a < BC::NC; ++a) jb[a * kJKThreads] = Real(0);
     if (q < tq && j < __ldg(M.ket_count + i)) {
       const int4 ki = M.ket.idx[j];
       const int nppk = M.ket.npp[j];
       const Real deg = Real((bi.z == bi.w ? 1 : 2) * (ki.z == ki.w ? 1 : 2) * ((P.same && i == j) ? 1 : 2));
       auto bra = [&](int f, int pp) -> Real { return sbra[pp * NFB + f]; };
-      static_for<KetChunks<KC, CS>::NCH>([&](auto Ch) {
-        constexpr int ch = decltype(Ch)::value;
-        Real out[BC::NC][CS];
-        quartet_chunk<Real, LA, LB, LC, LD, CS, ch>(out, bra, nppb, bs, ps, M.ket, j, nppk, sBoys, BK, P.boys64_T);
+#pragma unroll 1
+      for (int ch = cg; ch < KetChunks<KC, CS>::NCH; ch += ncg) {
+        quartet_chunk<Real, LA, LB, LC, LD, CS>(so, bra, nppb, bs, ps, M.ket, j, nppk, sBoys, BK, P.boys64_T, ch);
+        auto out = [&](int a, int cs) -> Real { return so[(a * CS + cs) * kJKThreads]; };
         // digestion (Eq. fock) of this chunk
 #pragma unroll
         for (int cs = 0; cs < CS; ++cs) {
           const int c = ch * CS + cs;
+          if (c >= KC::NC) break;
           const int lam = ki.x + c / KC::NB, sig = ki.y + c % KC::NB;
           // J_ket[la si] += sum_a D_ab v ; J_bra[a] += D_{la si} v
           const Real Dls = M.D[(size_t)lam * N + sig];
           Real jk = Real(0);
 #pragma unroll
           for (int a = 0; a < BC::NC; ++a) {
-            const Real v = deg * out[a][cs];
+            const Real v = deg * out(a, cs);
             jk = fma(sDab[a], v, jk);
-            jb[a] = fma(Dls, v, jb[a]);
+            jb[a * kJKThreads] = fma(Dls, v, jb[a * kJKThreads]);
           }
           atomicAdd(&M.J[(size_t)lam * N + sig], (double)jk);
           // K: (mu la) += D_nu si v ; (nu si) += D_mu la v ; (mu si) += D_nu la v ; (nu la) += D_mu si v
@@ -323,7 +347,7 @@ __global__ void __launch_bounds__(kJKThreads) jk_kernel(JKParams<Real> P) {
 #pragma unroll
             for (int ib = 0; ib < BC::NB; ++ib) {
               const int nu = bi.y + ib;
-              const Real v = deg * out[ia * BC::NB + ib][cs];
+              const Real v = deg * out(ia * BC::NB + ib, cs);
               k1 = fma(M.D[(size_t)nu * N + sig], v, k1);
               k3 = fma(M.D[(size_t)nu * N + lam], v, k3);
             }
@@ -337,7 +361,7 @@ __global__ void __launch_bounds__(kJKThreads) jk_kernel(JKParams<Real> P) {
 #pragma unroll
             for (int ia = 0; ia < BC::NA; ++ia) {
               const int mu = bi.x + ia;
-              const Real v = deg * out[ia * BC::NB + ib][cs];
+              const Real v = deg * out(ia * BC::NB + ib, cs);
               k2 = fma(M.D[(size_t)mu * N + lam], v, k2);
               k4 = fma(M.D[(size_t)mu * N + sig], v, k4);
             }
@@ -345,7 +369,7 @@ __global__ void __launch_bounds__(kJKThreads) jk_kernel(JKParams<Real> P) {
             atomicAdd(&M.K[(size_t)nu * N + lam], (double)k4);
           }
         }
-      });
+      }
     }
     // J_bra: warp reduction (every lane takes part, idle lanes hold zeros), one
     // shared-memory partial per warp and element, one FP64 global add per CTA
@@ -353,7 +377,7 @@ __global__ void __launch_bounds__(kJKThreads) jk_kernel(JKParams<Real> P) {
     const int warp = threadIdx.x >> 5;
 #pragma unroll
     for (int a = 0; a < BC::NC; ++a) {
-      Real v = jb[a];
+      Real v = jb[a * kJKThreads];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       if (lane == 0) sJw[warp * BC::NC + a] = v;
@@ -362,120 +386,6 @@ __global__ void __launch_bounds__(kJKThreads) jk_kernel(JKParams<Real> P) {
     for (int x = threadIdx.x; x < BC::NC; x += blockDim.x) {
       double v = 0.0;
       for (int w = 0; w < NWARP; ++w) v += (double)sJw[w * BC::NC + x];
-      atomicAdd(&M.J[(size_t)(bi.x + x / BC::NB) * N + bi.y + x % BC::NB], v);
-    }
-  }
-}
-
-// Chunk-warp variant for classes whose ket components span several register
-// chunks: a work item is (bra pair, tile of 32 kets, group of 4 chunks); warp w
-// of the CTA computes chunk 4*group + w for the 32 kets (lane = ket), so the
-// chunk index is uniform per warp and each warp runs the compile-time code of
-// its own chunk.  Parallelism grows by the number of chunks.
-constexpr int kCWKets = 32;
-constexpr int kCWWarps = kJKThreads / 32;
-
-template <typename Real, int LA, int LB, int LC, int LD, int CS>
-__global__ void __launch_bounds__(kJKThreads) jk_kernel_cw(JKParams<Real> P) {
-  using BC = PairCls<LA, LB>;
-  using KC = PairCls<LC, LD>;
-  constexpr int L = LA + LB + LC + LD;
-  constexpr int NFB = 4 + BC::NNZ;
-  constexpr int NCH = KetChunks<KC, CS>::NCH;
-  constexpr int NGRP = (NCH + kCWWarps - 1) / kCWWarps;
-  constexpr int BK = Boys<Real>::K, BR = Boys<Real>::NROW;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real* sBoys = reinterpret_cast<Real*>(smem_raw);
-  Real* sDab = reinterpret_cast<Real*>(smem_raw + (jk_boys_smem<Real>() + 15) / 16 * 16);
-  Real* sJw = sDab + BC::NC;
-  Real* sbra = sJw + kCWWarps * BC::NC;
-  for (int x = threadIdx.x; x < BR * BK; x += blockDim.x) sBoys[x] = P.boys[(x / BK) * kBoysCols + L + x % BK];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int item = blockIdx.x; item < P.nitems; item += gridDim.x) {
-    const JKMol<Real>& M = P.one;
-    const int N = M.N;
-    const int grp = item % NGRP, titem = item / NGRP;
-    const int i = find_bra(M.tile_prefix, M.bra.n, titem);
-    const int tile = titem - __ldg(M.tile_prefix + i);
-    const int4 bi = M.bra.idx[i];
-    const int nppb = M.bra.npp[i];
-    __syncthreads();
-    for (int x = threadIdx.x; x < nppb * NFB; x += blockDim.x) {
-      const int pp = x / NFB, f = x % NFB;
-      sbra[x] = M.bra.pd[((size_t)f * M.bra.ppmax + pp) * M.bra.n + i];
-    }
-    for (int x = threadIdx.x; x < BC::NC; x += blockDim.x) sDab[x] = M.D[(size_t)(bi.x + x / BC::NB) * N + bi.y + x % BC::NB];
-    __syncthreads();
-    const int j = tile * kCWKets + lane;
-    const int mych = grp * kCWWarps + warp;
-    Real jb[BC::NC];
-#pragma unroll
-    for (int a = 0; a < BC::NC; ++a) jb[a] = Real(0);
-    if (mych < NCH && j < __ldg(M.ket_count + i)) {
-      const int4 ki = M.ket.idx[j];
-      const int nppk = M.ket.npp[j];
-      const Real deg = Real((bi.z == bi.w ? 1 : 2) * (ki.z == ki.w ? 1 : 2) * ((P.same && i == j) ? 1 : 2));
-      auto bra = [&](int f, int pp) -> Real { return sbra[pp * NFB + f]; };
-      static_for<NCH>([&](auto Ch) {
-        constexpr int ch = decltype(Ch)::value;
-        if (ch != mych) return;  // warp-uniform
-        Real out[BC::NC][CS];
-        quartet_chunk<Real, LA, LB, LC, LD, CS, ch>(out, bra, nppb, 0, 1, M.ket, j, nppk, sBoys, BK, P.boys64_T);
-#pragma unroll
-        for (int cs = 0; cs < CS; ++cs) {
-          const int c = ch * CS + cs;
-          const int lam = ki.x + c / KC::NB, sig = ki.y + c % KC::NB;
-          const Real Dls = M.D[(size_t)lam * N + sig];
-          Real jk = Real(0);
-#pragma unroll
-          for (int a = 0; a < BC::NC; ++a) {
-            const Real v = deg * out[a][cs];
-            jk = fma(sDab[a], v, jk);
-            jb[a] = fma(Dls, v, jb[a]);
-          }
-          atomicAdd(&M.J[(size_t)lam * N + sig], (double)jk);
-#pragma unroll
-          for (int ia = 0; ia < BC::NA; ++ia) {
-            const int mu = bi.x + ia;
-            Real k1 = Real(0), k3 = Real(0);
-#pragma unroll
-            for (int ib = 0; ib < BC::NB; ++ib) {
-              const int nu = bi.y + ib;
-              const Real v = deg * out[ia * BC::NB + ib][cs];
-              k1 = fma(M.D[(size_t)nu * N + sig], v, k1);
-              k3 = fma(M.D[(size_t)nu * N + lam], v, k3);
-            }
-            atomicAdd(&M.K[(size_t)mu * N + lam], (double)k1);
-            atomicAdd(&M.K[(size_t)mu * N + sig], (double)k3);
-          }
-#pragma unroll
-          for (int ib = 0; ib < BC::NB; ++ib) {
-            const int nu = bi.y + ib;
-            Real k2 = Real(0), k4 = Real(0);
-#pragma unroll
-            for (int ia = 0; ia < BC::NA; ++ia) {
-              const int mu = bi.x + ia;
-              const Real v = deg * out[ia * BC::NB + ib][cs];
-              k2 = fma(M.D[(size_t)mu * N + lam], v, k2);
-              k4 = fma(M.D[(size_t)mu * N + sig], v, k4);
-            }
-            atomicAdd(&M.K[(size_t)nu * N + sig], (double)k2);
-            atomicAdd(&M.K[(size_t)nu * N + lam], (double)k4);
-          }
-        }
-      });
-    }
-#pragma unroll
-    for (int a = 0; a < BC::NC; ++a) {
-      Real v = jb[a];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) sJw[warp * BC::NC + a] = v;
-    }
-    __syncthreads();
-    for (int x = threadIdx.x; x < BC::NC; x += blockDim.x) {
-      double v = 0.0;
-      for (int w = 0; w < kCWWarps; ++w) v += (double)sJw[w * BC::NC + x];
       atomicAdd(&M.J[(size_t)(bi.x + x / BC::NB) * N + bi.y + x % BC::NB], v);
     }
   }

@@ -69,41 +69,6 @@ static cudaError_t dispatch_jk(int X, int Y, const JKParams<Real>& p, cudaStream
   return cudaErrorInvalidValue;
 }
 
-bool has_cw_variant(int X, int Y) {
-  switch (X * 8 + Y) {
-    case 18:
-    case 34:
-    case 35:
-    case 36:
-    case 41:
-    case 42:
-    case 43:
-    case 44:
-    case 45:
-      return true;
-  }
-  return false;
-}
-
-// Chunk-warp launches exist for FP32 classes with several ket chunks only.
-template <typename Real>
-static cudaError_t dispatch_jk_cw(int X, int Y, const JKParams<Real>& p, cudaStream_t s) {
-  if constexpr (std::is_same<Real, float>::value) {
-    switch (X * 8 + Y) {
-    case 18: return launch_jk_cw<float, 2, 2>(p, s);
-    case 34: return launch_jk_cw<float, 4, 2>(p, s);
-    case 35: return launch_jk_cw<float, 4, 3>(p, s);
-    case 36: return launch_jk_cw<float, 4, 4>(p, s);
-    case 41: return launch_jk_cw<float, 5, 1>(p, s);
-    case 42: return launch_jk_cw<float, 5, 2>(p, s);
-    case 43: return launch_jk_cw<float, 5, 3>(p, s);
-    case 44: return launch_jk_cw<float, 5, 4>(p, s);
-    case 45: return launch_jk_cw<float, 5, 5>(p, s);
-    }
-  }
-  return cudaErrorInvalidValue;
-}
-
 int run_list(fsim_basis* b, int X, int Y, const std::vector<int2>& items, double* d_out, int precision,
              cudaStream_t s) {
   if (precision != FSIM_FP64) {
@@ -166,15 +131,20 @@ static long long screened_counts(const fsim_basis* b, int X, int Y, double tau, 
   return nq;
 }
 
-// (Re)build the device work list of one class pair for a launch shape:
-// psplit threads per quartet on the unrolled kernel, or the cooperative kernel.
+// (Re)build the device work list of one class pair for a launch shape: on the
+// unrolled kernel psplit threads per quartet share the bra primitive pairs and
+// csplit thread groups share the ket chunks; or the cooperative kernel.
 int set_class_plan(fsim_basis* b, int X, int Y, const std::vector<int>& count, int psplit, int coop,
-                   ClassPairPlan& cp, int cw) {
+                   ClassPairPlan& cp, int csplit) {
   const DevClass& CX = b->cls[X];
-  cp.cw = (cw && !coop) ? 1 : 0;
-  cp.psplit = (coop || cp.cw) ? 1 : psplit;
+  if (!coop && !(psplit >= 1 && psplit <= kJKThreads / 4 && (csplit == 1 || csplit == 2 || csplit == 4))) {
+    set_error("bad launch shape (%d|%d): psplit %d, csplit %d", X, Y, psplit, csplit);
+    return FSIM_EINVAL;
+  }
   cp.coop = coop;
-  cp.tq = coop ? kCoopWarps : (cp.cw ? kCWKets : kJKThreads / cp.psplit);
+  cp.psplit = coop ? 1 : psplit;
+  cp.csplit = coop ? 1 : csplit;
+  cp.tq = coop ? kCoopWarps : (kJKThreads / cp.csplit) / cp.psplit;
   std::vector<int> prefix(CX.n + 1, 0);
   for (int i = 0; i < CX.n; ++i) prefix[i + 1] = prefix[i] + (count[i] + cp.tq - 1) / cp.tq;
   cp.nitems = prefix[CX.n];
@@ -212,17 +182,22 @@ int get_plan(fsim_basis* b, double tau, int shard, int nshards, int precision, F
       cp.nquartets = screened_counts(b, X, Y, tau, shard, nshards, count);
       const int L = pair_cls_la(X) + pair_cls_lb(X) + pair_cls_la(Y) + pair_cls_lb(Y);
       const int coop = (precision == FSIM_FP64 && L >= kCoopMinL64) ? 1 : 0;
-      int ps = 1, cw = 0;
+      int ps = 1, cs = 1;
       if (!coop) {
         if (psplit_force > 0) {
           ps = std::min(psplit_force, CX.ppmax);
         } else {
+          // few quartets: split bra primitive pairs, then ket chunks, until
+          // one launch has about two CTAs' worth of threads per SM
           const long long target = (long long)device_sm_count() * 2 * kJKThreads;
           for (int c : {3, 9})
             if (cp.nquartets * ps < target && c <= CX.ppmax) ps = c;
+          const int nch = precision == FSIM_FP64 ? jk_chunks<double>(X, Y) : jk_chunks<float>(X, Y);
+          for (int c : {2, 4})
+            if (cp.nquartets * ps * cs < target && c <= nch) cs = c;
         }
       }
-      FSIM_TRY(set_class_plan(b, X, Y, count, ps, coop, cp, cw));
+      FSIM_TRY(set_class_plan(b, X, Y, count, ps, coop, cp, cs));
       P->nquartets += cp.nquartets;
     }
   *out = P;
@@ -251,9 +226,116 @@ int ensure_scratch(fsim_basis* b) {
   return FSIM_OK;
 }
 
+// One class pair's launch with the shape its plan entry holds; J/K
+// accumulators passed in (the basis's own or caller-supplied scratch).
+template <typename Real>
+static cudaError_t launch_cp(fsim_basis* b, int X, int Y, const ClassPairPlan& cp, const Real* Dr, double* Jacc,
+                             double* Kacc, float boys64_T, cudaStream_t s) {
+  const Real* boys = std::is_same<Real, double>::value ? (const Real*)b->d_boys64 : (const Real*)b->d_boys32;
+  if (cp.nitems == 0) return cudaSuccess;
+  if (cp.coop) {
+    CoopParams<Real> p{};
+    p.bra = b->cls[X].view<Real>();
+    p.ket = b->cls[Y].view<Real>();
+    make_cls_desc(X, p.bd);
+    make_cls_desc(Y, p.kd);
+    p.same = X == Y ? 1 : 0;
+    p.list_mode = 0;
+    p.tile_prefix = cp.d_prefix;
+    p.ket_count = cp.d_count;
+    p.tq = cp.tq;
+    p.nitems = cp.nitems;
+    p.N = b->nbf;
+    p.D = Dr;
+    p.J = Jacc;
+    p.K = Kacc;
+    p.boys = boys;
+    p.boys64_T = boys64_T;
+    return launch_coop<Real>(p, cp.nitems, s);
+  }
+  JKParams<Real> p{};
+  p.one = JKMol<Real>{b->cls[X].view<Real>(), b->cls[Y].view<Real>(), cp.d_prefix, cp.d_count, b->nbf, Dr, Jacc, Kacc};
+  p.nitems = cp.nitems;
+  p.same = X == Y ? 1 : 0;
+  p.psplit = cp.psplit;
+  p.csplit = cp.csplit;
+  p.bra_ppmax = b->cls[X].ppmax;
+  p.boys = boys;
+  p.boys64_T = boys64_T;
+  return dispatch_jk<Real>(X, Y, p, s);
+}
+
+// Relative cost of one quartet of a class pair: the algorithmic flop count per
+// primitive quartet (R recursion + the cheaper contraction order).
+static double class_cost(int X, int Y) {
+  const int la = pair_cls_la(X), lb = pair_cls_lb(X), lc = pair_cls_la(Y), ld = pair_cls_lb(Y);
+  const double A = ncart(la) * ncart(lb), C = ncart(lc) * ncart(ld);
+  const double H1 = nherm(la + lb), H2 = nherm(lc + ld);
+  double r = 0.0;
+  for (int n = 0; n <= la + lb + lc + ld; ++n) r += nherm(n);
+  return 2.0 * r + 2.0 * std::min(A * H1 * H2 + A * C * H2, C * H1 * H2 + A * C * H1) + 16.0;
+}
+
+static int ensure_aux_streams(fsim_basis* b) {
+  if (b->aux_ok) return FSIM_OK;
+  for (int k = 0; k < fsim_basis::kAuxStreams; ++k) {
+    FSIM_CK(cudaStreamCreateWithFlags(&b->aux[k], cudaStreamNonBlocking));
+    FSIM_CK(cudaEventCreateWithFlags(&b->join_ev[k], cudaEventDisableTiming));
+  }
+  FSIM_CK(cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming));
+  b->aux_ok = true;
+  return FSIM_OK;
+}
+
+// The class-pair launches of one build.  Timed builds run them one after the
+// other on s (per-class events); otherwise they are spread over s and the
+// auxiliary streams, longest first onto the least loaded stream, between a
+// fork and a join event on s, so that the short launches and the tails of the
+// long ones overlap.  All launches add into the same accumulators (atomics).
 template <typename Real>
 static int launch_all(fsim_basis* b, FockPlan* plan, const Real* Dr, float boys64_T, bool timing, cudaStream_t s) {
-  const Real* boys = std::is_same<Real, double>::value ? (const Real*)b->d_boys64 : (const Real*)b->d_boys32;
+  if (!timing) {
+    FSIM_TRY(ensure_aux_streams(b));
+    struct Job {
+      int X, Y;
+      double cost;
+    };
+    std::vector<Job> jobs;
+    for (int X = kNumPairCls - 1; X >= 0; --X)
+      for (int Y = X; Y >= 0; --Y) {
+        const ClassPairPlan& cp = plan->cp[X][Y];
+        const int ci = X * kNumPairCls + Y;
+        b->last_class_q[ci] = cp.nquartets;
+        b->last_class_run[ci] = cp.nitems > 0;
+        if (cp.nitems > 0) jobs.push_back(Job{X, Y, (double)cp.nquartets * class_cost(X, Y)});
+      }
+    std::stable_sort(jobs.begin(), jobs.end(), [](const Job& a, const Job& c) { return a.cost > c.cost; });
+    constexpr int NS = fsim_basis::kAuxStreams + 1;
+    cudaStream_t st[NS] = {s};
+    for (int k = 0; k < fsim_basis::kAuxStreams; ++k) st[k + 1] = b->aux[k];
+    const int nuse = std::min<int>(NS, (int)jobs.size());
+    FSIM_CK(cudaEventRecord(b->fork_ev, s));
+    for (int k = 1; k < nuse; ++k) FSIM_CK(cudaStreamWaitEvent(st[k], b->fork_ev, 0));
+    double load[NS] = {};
+    for (const Job& j : jobs) {
+      int k = 0;
+      for (int t = 1; t < nuse; ++t)
+        if (load[t] < load[k]) k = t;
+      load[k] += j.cost;
+      ++b->last_launches;
+      const cudaError_t e = launch_cp<Real>(b, j.X, j.Y, plan->cp[j.X][j.Y], Dr, b->d_Jacc, b->d_Kacc, boys64_T,
+                                            st[k]);
+      if (e != cudaSuccess) {
+        set_error("J/K kernel (%d|%d): %s", j.X, j.Y, cudaGetErrorString(e));
+        return FSIM_ECUDA;
+      }
+    }
+    for (int k = 1; k < nuse; ++k) {
+      FSIM_CK(cudaEventRecord(b->join_ev[k - 1], st[k]));
+      FSIM_CK(cudaStreamWaitEvent(s, b->join_ev[k - 1], 0));
+    }
+    return FSIM_OK;
+  }
   for (int X = kNumPairCls - 1; X >= 0; --X)
     for (int Y = X; Y >= 0; --Y) {
       const ClassPairPlan& cp = plan->cp[X][Y];
@@ -263,38 +345,7 @@ static int launch_all(fsim_basis* b, FockPlan* plan, const Real* Dr, float boys6
       if (cp.nitems == 0) continue;
       ++b->last_launches;
       if (timing) FSIM_CK(cudaEventRecord(b->ev[ci][0], s));
-      cudaError_t e;
-      if (cp.coop) {
-        CoopParams<Real> p{};
-        p.bra = b->cls[X].view<Real>();
-        p.ket = b->cls[Y].view<Real>();
-        make_cls_desc(X, p.bd);
-        make_cls_desc(Y, p.kd);
-        p.same = X == Y ? 1 : 0;
-        p.list_mode = 0;
-        p.tile_prefix = cp.d_prefix;
-        p.ket_count = cp.d_count;
-        p.tq = cp.tq;
-        p.nitems = cp.nitems;
-        p.N = b->nbf;
-        p.D = Dr;
-        p.J = b->d_Jacc;
-        p.K = b->d_Kacc;
-        p.boys = boys;
-        p.boys64_T = boys64_T;
-        e = launch_coop<Real>(p, cp.nitems, s);
-      } else {
-        JKParams<Real> p{};
-        p.one = JKMol<Real>{b->cls[X].view<Real>(), b->cls[Y].view<Real>(), cp.d_prefix, cp.d_count, b->nbf, Dr,
-                            b->d_Jacc, b->d_Kacc};
-        p.nitems = cp.nitems;
-        p.same = X == Y ? 1 : 0;
-        p.psplit = cp.psplit;
-        p.bra_ppmax = b->cls[X].ppmax;
-        p.boys = boys;
-        p.boys64_T = boys64_T;
-        e = cp.cw ? dispatch_jk_cw<Real>(X, Y, p, s) : dispatch_jk<Real>(X, Y, p, s);
-      }
+      const cudaError_t e = launch_cp<Real>(b, X, Y, cp, Dr, b->d_Jacc, b->d_Kacc, boys64_T, s);
       if (e != cudaSuccess) {
         set_error("J/K kernel (%d|%d): %s", X, Y, cudaGetErrorString(e));
         return FSIM_ECUDA;
@@ -575,43 +626,9 @@ namespace fsim {
 template <typename Real>
 static int launch_all_into(fsim_basis* b, FockPlan* plan, const Real* Dr, float boys64_T, double* Jacc,
                            double* Kacc, cudaStream_t s) {
-  const Real* boys = std::is_same<Real, double>::value ? (const Real*)b->d_boys64 : (const Real*)b->d_boys32;
   for (int X = kNumPairCls - 1; X >= 0; --X)
     for (int Y = X; Y >= 0; --Y) {
-      const ClassPairPlan& cp = plan->cp[X][Y];
-      if (cp.nitems == 0) continue;
-      cudaError_t e;
-      if (cp.coop) {
-        CoopParams<Real> p{};
-        p.bra = b->cls[X].view<Real>();
-        p.ket = b->cls[Y].view<Real>();
-        make_cls_desc(X, p.bd);
-        make_cls_desc(Y, p.kd);
-        p.same = X == Y ? 1 : 0;
-        p.list_mode = 0;
-        p.tile_prefix = cp.d_prefix;
-        p.ket_count = cp.d_count;
-        p.tq = cp.tq;
-        p.nitems = cp.nitems;
-        p.N = b->nbf;
-        p.D = Dr;
-        p.J = Jacc;
-        p.K = Kacc;
-        p.boys = boys;
-        p.boys64_T = boys64_T;
-        e = launch_coop<Real>(p, cp.nitems, s);
-      } else {
-        JKParams<Real> p{};
-        p.one = JKMol<Real>{b->cls[X].view<Real>(), b->cls[Y].view<Real>(), cp.d_prefix, cp.d_count, b->nbf, Dr,
-                            Jacc, Kacc};
-        p.nitems = cp.nitems;
-        p.same = X == Y ? 1 : 0;
-        p.psplit = cp.psplit;
-        p.bra_ppmax = b->cls[X].ppmax;
-        p.boys = boys;
-        p.boys64_T = boys64_T;
-        e = cp.cw ? dispatch_jk_cw<Real>(X, Y, p, s) : dispatch_jk<Real>(X, Y, p, s);
-      }
+      const cudaError_t e = launch_cp<Real>(b, X, Y, plan->cp[X][Y], Dr, Jacc, Kacc, boys64_T, s);
       if (e != cudaSuccess) {
         set_error("J/K kernel (%d|%d): %s", X, Y, cudaGetErrorString(e));
         return FSIM_ECUDA;
@@ -672,42 +689,6 @@ int fock_build_into(fsim_basis* b, const double* dD, double* dJ, double* dK, con
 
 namespace fsim {
 
-// One class pair's launch with an explicit plan entry (autotuner).
-template <typename Real>
-static cudaError_t launch_cp(fsim_basis* b, int X, int Y, const ClassPairPlan& cp, const Real* Dr, double* Jacc,
-                             double* Kacc, float b64, cudaStream_t s) {
-  const Real* boys = std::is_same<Real, double>::value ? (const Real*)b->d_boys64 : (const Real*)b->d_boys32;
-  if (cp.nitems == 0) return cudaSuccess;
-  if (cp.coop) {
-    CoopParams<Real> p{};
-    p.bra = b->cls[X].view<Real>();
-    p.ket = b->cls[Y].view<Real>();
-    make_cls_desc(X, p.bd);
-    make_cls_desc(Y, p.kd);
-    p.same = X == Y ? 1 : 0;
-    p.tile_prefix = cp.d_prefix;
-    p.ket_count = cp.d_count;
-    p.tq = cp.tq;
-    p.nitems = cp.nitems;
-    p.N = b->nbf;
-    p.D = Dr;
-    p.J = Jacc;
-    p.K = Kacc;
-    p.boys = boys;
-    p.boys64_T = b64;
-    return launch_coop<Real>(p, cp.nitems, s);
-  }
-  JKParams<Real> p{};
-  p.one = JKMol<Real>{b->cls[X].view<Real>(), b->cls[Y].view<Real>(), cp.d_prefix, cp.d_count, b->nbf, Dr, Jacc, Kacc};
-  p.nitems = cp.nitems;
-  p.same = X == Y ? 1 : 0;
-  p.psplit = cp.psplit;
-  p.bra_ppmax = b->cls[X].ppmax;
-  p.boys = boys;
-  p.boys64_T = b64;
-  return cp.cw ? dispatch_jk_cw<Real>(X, Y, p, s) : dispatch_jk<Real>(X, Y, p, s);
-}
-
 template <typename Real>
 static int autotune_impl(fsim_basis* b, FockPlan* plan, const Real* Dr, float b64, cudaStream_t s, int* choice,
                          float* best_ms) {
@@ -724,20 +705,21 @@ static int autotune_impl(fsim_basis* b, FockPlan* plan, const Real* Dr, float b6
       screened_counts(b, X, Y, plan->tau, plan->shard, plan->nshards, count);
       const int L = pair_cls_la(X) + pair_cls_lb(X) + pair_cls_la(Y) + pair_cls_lb(Y);
       struct Cand {
-        int psplit, coop, cw;
+        int psplit, coop, csplit;
       };
       std::vector<Cand> cands;
       const bool unrolled_ok = !(std::is_same<Real, double>::value && L >= kCoopMinL64);
+      const int nch = jk_chunks<Real>(X, Y);
       if (unrolled_ok)
         for (int ps : {1, 3, 9})
-          if (ps <= b->cls[X].ppmax) cands.push_back({ps, 0, 0});
-      if (std::is_same<Real, float>::value && has_cw_variant(X, Y)) cands.push_back({1, 0, 1});
-      cands.push_back({1, 1, 0});
+          for (int cs : {1, 2, 4})
+            if (ps <= b->cls[X].ppmax && cs <= nch) cands.push_back({ps, 0, cs});
+      cands.push_back({1, 1, 1});
       float best = 1e30f;
       Cand win = cands[0];
       ClassPairPlan tmp;
       for (const Cand& c : cands) {
-        if ((rc = set_class_plan(b, X, Y, count, c.psplit, c.coop, tmp, c.cw)) != FSIM_OK) break;
+        if ((rc = set_class_plan(b, X, Y, count, c.psplit, c.coop, tmp, c.csplit)) != FSIM_OK) break;
         float t[3];
         cudaError_t e = launch_cp<Real>(b, X, Y, tmp, Dr, b->d_Jacc, b->d_Kacc, b64, s);  // warm-up
         for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
@@ -761,8 +743,8 @@ static int autotune_impl(fsim_basis* b, FockPlan* plan, const Real* Dr, float b6
       dev_free(tmp.d_prefix);
       dev_free(tmp.d_count);
       if (rc != FSIM_OK) break;
-      rc = set_class_plan(b, X, Y, count, win.psplit, win.coop, cp, win.cw);
-      if (choice) choice[ci] = win.coop ? -1 : (win.cw ? -2 : win.psplit);
+      rc = set_class_plan(b, X, Y, count, win.psplit, win.coop, cp, win.csplit);
+      if (choice) choice[ci] = win.coop ? -1 : 10 * win.psplit + win.csplit;
       if (best_ms) best_ms[ci] = best;
     }
   cudaEventDestroy(e0);

@@ -78,14 +78,66 @@ inline PairView<float> DevClass::view<float>() const {
   return PairView<float>{n, ppmax, idx, npp, pd32, pq32};
 }
 
+// Ket components per register chunk.  The per-thread registers of the unrolled
+// kernel hold R (nherm(L)), the chunk's W (bra Hermite terms x CS) and the
+// chunk's E non-zeros; the quartet block itself lives in shared memory.  The
+// largest chunk whose estimate fits kChunkRegBudget is taken (the last chunk
+// may be shorter).
+// FP64 kernels keep the whole quartet in one chunk: GB300 issues FP64 FMAs at a
+// small fraction of the FP32 rate, so arrays that overflow into L1-resident
+// local memory do not limit them, while chunking would repeat the Hermite
+// recursion per chunk.
+#ifndef FSIM_CHUNK_REG_BUDGET
+#define FSIM_CHUNK_REG_BUDGET 170
+#endif
+constexpr int kChunkRegBudget = FSIM_CHUNK_REG_BUDGET;
+
+__host__ __device__ constexpr int pair_comp_nnz(int la, int lb, int c) {
+  int p = 1;
+  for (int ax = 0; ax < 3; ++ax) p *= cart_comp(la, c / ncart(lb), ax) + cart_comp(lb, c % ncart(lb), ax) + 1;
+  return p;
+}
+
+__host__ __device__ constexpr int chunk_nnz_max(int lc, int ld, int cs) {
+  const int C = ncart(lc) * ncart(ld);
+  int m = 0;
+  for (int c0 = 0; c0 < C; c0 += cs) {
+    int z = 0;
+    for (int c = c0; c < c0 + cs && c < C; ++c) z += pair_comp_nnz(lc, ld, c);
+    m = z > m ? z : m;
+  }
+  return m;
+}
+
+template <typename Real>
+__host__ __device__ constexpr int chunk_size(int X, int Y) {
+  const int lc = pair_cls_la(Y), ld = pair_cls_lb(Y);
+  const int C = ncart(lc) * ncart(ld);
+  if (sizeof(Real) == 8) return C;
+  const int H1 = nherm(pair_cls_la(X) + pair_cls_lb(X));
+  const int NH = nherm(pair_cls_la(X) + pair_cls_lb(X) + lc + ld);
+  for (int cs = C; cs > 1; --cs)
+    if (NH + H1 * cs + chunk_nnz_max(lc, ld, cs) <= kChunkRegBudget) {
+      const int nch = (C + cs - 1) / cs;
+      return (C + nch - 1) / nch;  // same chunk count, balanced sizes
+    }
+  return 1;
+}
+
+// Ket chunks of the unrolled kernel for a class pair (host side of KetChunks).
+template <typename Real>
+__host__ __device__ constexpr int jk_chunks(int X, int Y) {
+  return (ncart(pair_cls_la(Y)) * ncart(pair_cls_lb(Y)) + chunk_size<Real>(X, Y) - 1) / chunk_size<Real>(X, Y);
+}
+
 // Screened work list of one class pair (bra class X >= ket class Y).
 struct ClassPairPlan {
   int nbra = 0;
   int nitems = 0;
   long long nquartets = 0;
   int psplit = 1;
+  int csplit = 1;           // ket chunk groups per CTA (unrolled kernel)
   int coop = 0;             // 1: warp-cooperative table-driven kernel
-  int cw = 0;               // 1: chunk-warp variant of the unrolled kernel (FP32)
   int tq = kJKThreads;      // kets per work item
   int* d_prefix = nullptr;  // [nbra + 1]
   int* d_count = nullptr;   // [nbra]
@@ -104,8 +156,6 @@ struct FockPlan {
 // Kernel launchers (explicit instantiations in eri_inst_*.cu).
 template <typename Real, int X, int Y>
 cudaError_t launch_jk(const JKParams<Real>& p, cudaStream_t s);
-template <typename Real, int X, int Y>
-cudaError_t launch_jk_cw(const JKParams<Real>& p, cudaStream_t s);
 template <typename Real>
 struct CoopParams;
 template <typename Real>
@@ -154,13 +204,17 @@ struct fsim_basis {
   long long last_class_q[fsim::kNumPairCls * fsim::kNumPairCls] = {};
   bool last_class_run[fsim::kNumPairCls * fsim::kNumPairCls] = {};
   cudaStream_t last_stream = nullptr;
+  // auxiliary streams of the concurrent class-pair launches (created on first use)
+  static constexpr int kAuxStreams = 3;
+  cudaStream_t aux[kAuxStreams] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[kAuxStreams] = {};
+  bool aux_ok = false;
 };
 
 namespace fsim {
 int get_plan(fsim_basis* b, double tau, int shard, int nshards, int precision, FockPlan** out, int psplit_force);
 int set_class_plan(fsim_basis* b, int X, int Y, const std::vector<int>& count, int psplit, int coop,
-                   ClassPairPlan& cp, int cw = 0);
-bool has_cw_variant(int X, int Y);
+                   ClassPairPlan& cp, int csplit = 1);
 int ensure_scratch(fsim_basis* b);
 int ensure_schwarz(fsim_basis* b);
 int device_sm_count();

@@ -1,0 +1,82 @@
+"""Time Fock builds (and optionally the SCF) of one synthetic workload.
+
+    python -m paper_2510_24968_gb300.time_fock --workload cloud60 --tau 1e-11 --precision mixed
+
+Prints one JSON object: per precision the build time of each repetition
+(CUDA events on the launching stream), the screened unique quartet count,
+quartets/s and the per-class-pair kernel times of a separate timed build.
+Every step runs in libfsim; this module only draws the seeded density and
+reads the results.  Also the fixed command line used for kernel profiles.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from fsim_synth import workload
+
+from .fsim import FSIM_FP64, FSIM_MIXED, Basis
+
+_NAMES = ["ss", "ps", "pp", "ds", "dp", "dd"]
+
+
+def main(argv=None):
+    import torch
+
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--workload", default="water8")
+    ap.add_argument("--tau", type=float, default=1e-10)
+    ap.add_argument("--precision", choices=["mixed", "fp64", "both"], default="mixed")
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--tune", action="store_true", help="autotune launch shapes first")
+    ap.add_argument("--boys-fp64-T", type=float, default=0.0)
+    ap.add_argument("--scf", action="store_true", help="also run the SCF to convergence")
+    a = ap.parse_args(argv)
+
+    mol = workload(a.workload)
+    t0 = time.perf_counter()
+    gb = Basis(mol)
+    gb.schwarz()
+    torch.cuda.synchronize()
+    out = {"workload": a.workload, "nbf": gb.nbf, "nshell": mol.nshell, "tau": a.tau,
+           "setup_s": time.perf_counter() - t0}
+    N = gb.nbf
+    Dn = np.random.default_rng(0).standard_normal((N, N)) * 0.02
+    D = torch.from_numpy(Dn + Dn.T).cuda()
+    J, K = torch.zeros_like(D), torch.zeros_like(D)
+    precs = {"mixed": [FSIM_MIXED], "fp64": [FSIM_FP64], "both": [FSIM_MIXED, FSIM_FP64]}[a.precision]
+    for prec in precs:
+        name = "mixed" if prec == FSIM_MIXED else "fp64"
+        kw = dict(tau=a.tau, precision=prec, boys_fp64_T=a.boys_fp64_T)
+        if a.tune:
+            tuned = gb.autotune(tau=a.tau, precision=prec)
+            out[f"{name}_autotune"] = {f"{_NAMES[x]}|{_NAMES[y]}": c for (x, y), (c, _) in tuned.items()}
+        gb.fock_build(D, J, K, **kw)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(a.reps):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            gb.fock_build(D, J, K, **kw)
+            e.record()
+            torch.cuda.synchronize()
+            ts.append(s.elapsed_time(e))
+        q = gb.last_quartet_count()
+        gb.fock_build(D, J, K, timing=True, **kw)
+        ms, qs, nl = gb.last_class_times()
+        out[name] = {"build_ms": ts, "quartets": q, "quartets_per_s": q / (min(ts) * 1e-3),
+                     "class_ms": {f"{_NAMES[x]}|{_NAMES[y]}": round(v, 4) for (x, y), v in ms.items()},
+                     "launches": nl}
+        if a.scf:
+            t0 = time.perf_counter()
+            r = gb.scf(precision=prec, tau=a.tau)
+            out[name]["scf"] = {"e_total": r["e_total"], "iters": r["iters"], "converged": bool(r["converged"]),
+                                "wall_s": time.perf_counter() - t0}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -89,6 +89,30 @@ def test_eri_blocks_sampled_full_size_cluster():
         assert np.abs(blk - ref).max() < 1e-10, q
 
 
+
+def test_eri_blocks_sampled_organic_cloud():
+    # organic cloud of 60 heavy atoms (1140 Cartesian functions): a seeded sample of
+    # 10^5 shell quartets drawn uniformly, plus 8 quartets of every (la lb|lc ld)
+    # combination drawn among shells of neighbouring atoms, FP64 blocks one by one
+    mol = workload("cloud60")
+    gb, ob = _pair(mol)
+    ls = np.array([s.l for s in mol.shells])
+    rng = np.random.default_rng(21)
+    quartets = rng.integers(0, mol.nshell, size=(100000, 4))
+    xyz = np.asarray(mol.xyz)[[s.atom for s in mol.shells]]
+    extra = []
+    for combo in np.ndindex(3, 3, 3, 3):
+        for _ in range(8):
+            a = int(rng.choice(np.flatnonzero(ls == combo[0])))
+            near = np.linalg.norm(xyz - xyz[a], axis=1) < 6.0
+            extra.append([a] + [int(rng.choice(np.flatnonzero((ls == l) & near))) for l in combo[1:]])
+    quartets = np.concatenate([quartets, np.array(extra)]).astype(np.int32)
+    got = gb.eri_quartets(quartets)
+    ref = ob.eri_blocks(quartets)
+    err = max(float(np.abs(g - r).max()) for g, r in zip(got, ref))
+    assert err < 1e-10, err
+
+
 # ------------------------------------------------------------------ J / K
 @pytest.mark.parametrize("tau", [0.0, 1e-10, 1e-4])
 def test_jk_fp64_water(tau):
@@ -253,3 +277,28 @@ def test_scf_full_size_cluster_energy():
     rmx = gb.scf(precision=FSIM_MIXED, tau=1e-10)
     assert rmx["converged"] and abs(rmx["e_total"] - gold["e_total"]) < 1e-8
     assert rmx["time_s"] < r64["time_s"]
+
+
+def test_jk_sampled_blocks_organic_cloud():
+    # organic cloud of 12 heavy atoms, tau 1e-11: sampled J/K blocks by definition;
+    # FP64 within 1e-10, mixed (FP32 Boys everywhere, or FP64 Boys above T = 30)
+    # within 2e-6 of max|J|
+    from paper_2510_24968_gb300 import FSIM_FP64, FSIM_MIXED
+    mol = workload("cloud12")
+    gb, ob = _pair(mol)
+    D = _rand_sym(gb.nbf, 12) * 0.05
+    Q = ob.schwarz()
+    J, K = gb.fock_build(D, tau=1e-11, precision=FSIM_FP64)
+    mixed = [gb.fock_build(D, tau=1e-11, precision=FSIM_MIXED, boys_fp64_T=t) for t in (0.0, 30.0)]
+    ls = [s.l for s in mol.shells]
+    ao = np.cumsum([0] + [(l + 1) * (l + 2) // 2 for l in ls])
+    d_shells = [i for i, l in enumerate(ls) if l == 2]
+    p_shells = [i for i, l in enumerate(ls) if l == 1]
+    s_shells = [i for i, l in enumerate(ls) if l == 0]
+    scale = np.abs(J).max()
+    for sa, sb in [(d_shells[2], d_shells[7]), (p_shells[5], d_shells[0]), (s_shells[3], s_shells[20])]:
+        Jb, Kb = ob.jk_block(D, sa, sb, tau=1e-11, Q=Q)
+        sl = (slice(ao[sa], ao[sa + 1]), slice(ao[sb], ao[sb + 1]))
+        assert np.abs(J[sl] - Jb).max() < 1e-10 and np.abs(K[sl] - Kb).max() < 1e-10
+        for Jm, Km in mixed:
+            assert np.abs(Jm[sl] - Jb).max() < 2e-6 * scale and np.abs(Km[sl] - Kb).max() < 2e-6 * scale
