@@ -22,50 +22,37 @@
 #include <cstring>
 #include <vector>
 
-#include "coop.cuh"
 #include "fsim_internal.h"
 
 namespace fsim {
 
-extern template cudaError_t launch_coop<double>(const CoopParams<double>&, int, cudaStream_t);
-extern template cudaError_t launch_coop<float>(const CoopParams<float>&, int, cudaStream_t);
 
 namespace {
-
-template <typename Real, int X, int Y>
-cudaError_t jk_if(const JKParams<Real>& p, cudaStream_t s) {
-  constexpr int L = pair_cls_la(X) + pair_cls_lb(X) + pair_cls_la(Y) + pair_cls_lb(Y);
-  if constexpr (std::is_same<Real, double>::value && L >= kCoopMinL64) {
-    return cudaErrorInvalidValue;
-  } else {
-    return launch_jk<Real, X, Y>(p, s);
-  }
-}
 
 template <typename Real>
 cudaError_t dispatch(int X, int Y, const JKParams<Real>& p, cudaStream_t s) {
   switch (X * 8 + Y) {
-    case 0: return jk_if<Real, 0, 0>(p, s);
-    case 8: return jk_if<Real, 1, 0>(p, s);
-    case 9: return jk_if<Real, 1, 1>(p, s);
-    case 16: return jk_if<Real, 2, 0>(p, s);
-    case 17: return jk_if<Real, 2, 1>(p, s);
-    case 18: return jk_if<Real, 2, 2>(p, s);
-    case 24: return jk_if<Real, 3, 0>(p, s);
-    case 25: return jk_if<Real, 3, 1>(p, s);
-    case 26: return jk_if<Real, 3, 2>(p, s);
-    case 27: return jk_if<Real, 3, 3>(p, s);
-    case 32: return jk_if<Real, 4, 0>(p, s);
-    case 33: return jk_if<Real, 4, 1>(p, s);
-    case 34: return jk_if<Real, 4, 2>(p, s);
-    case 35: return jk_if<Real, 4, 3>(p, s);
-    case 36: return jk_if<Real, 4, 4>(p, s);
-    case 40: return jk_if<Real, 5, 0>(p, s);
-    case 41: return jk_if<Real, 5, 1>(p, s);
-    case 42: return jk_if<Real, 5, 2>(p, s);
-    case 43: return jk_if<Real, 5, 3>(p, s);
-    case 44: return jk_if<Real, 5, 4>(p, s);
-    case 45: return jk_if<Real, 5, 5>(p, s);
+    case 0: return launch_jk<Real, 0, 0>(p, s);
+    case 8: return launch_jk<Real, 1, 0>(p, s);
+    case 9: return launch_jk<Real, 1, 1>(p, s);
+    case 16: return launch_jk<Real, 2, 0>(p, s);
+    case 17: return launch_jk<Real, 2, 1>(p, s);
+    case 18: return launch_jk<Real, 2, 2>(p, s);
+    case 24: return launch_jk<Real, 3, 0>(p, s);
+    case 25: return launch_jk<Real, 3, 1>(p, s);
+    case 26: return launch_jk<Real, 3, 2>(p, s);
+    case 27: return launch_jk<Real, 3, 3>(p, s);
+    case 32: return launch_jk<Real, 4, 0>(p, s);
+    case 33: return launch_jk<Real, 4, 1>(p, s);
+    case 34: return launch_jk<Real, 4, 2>(p, s);
+    case 35: return launch_jk<Real, 4, 3>(p, s);
+    case 36: return launch_jk<Real, 4, 4>(p, s);
+    case 40: return launch_jk<Real, 5, 0>(p, s);
+    case 41: return launch_jk<Real, 5, 1>(p, s);
+    case 42: return launch_jk<Real, 5, 2>(p, s);
+    case 43: return launch_jk<Real, 5, 3>(p, s);
+    case 44: return launch_jk<Real, 5, 4>(p, s);
+    case 45: return launch_jk<Real, 5, 5>(p, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -115,7 +102,7 @@ struct fsim_batch {
   double tau = 0.0;
   cudaStream_t s = nullptr;
   struct CPB {
-    int nitems = 0, coop = 0, bra_ppmax = 1, nin = 0;
+    int nitems = 0, bra_ppmax = 1, nin = 0;
     void* d_mols = nullptr;
     int* d_prefix = nullptr;
     int* d_ids = nullptr;
@@ -147,7 +134,6 @@ int build_tables(fsim_batch* bt, int prec) {
         FSIM_TRY(get_plan(b, bt->tau, 0, 1, prec == 0 ? FSIM_FP64 : FSIM_MIXED, &plan, 1));
         const ClassPairPlan& cp = plan->cp[X][Y];
         if (cp.nitems == 0) continue;
-        C.coop = cp.coop;
         const Real* D = prec == 0 ? (const Real*)bt->h_ptrs[m].Din : (const Real*)bt->h_ptrs[m].D32;
         mols.push_back(JKMol<Real>{b->cls[X].view<Real>(), b->cls[Y].view<Real>(), cp.d_prefix, cp.d_count, b->nbf,
                                    D, b->d_Jacc, b->d_Kacc});
@@ -181,34 +167,7 @@ int launch_batch(fsim_batch* bt, int prec, cudaStream_t s) {
       const fsim_batch::CPB& C = bt->cp[prec][X][Y];
       if (C.nin == 0) continue;
       cudaError_t e = cudaSuccess;
-      if (C.coop) {
-        // cooperative classes: one launch per molecule (inactive molecules are
-        // skipped by the host before capture would freeze them, so they run;
-        // their accumulators are never symmetrised)
-        for (int t = 0; t < C.nin && e == cudaSuccess; ++t) {
-          fsim_basis* b = bt->b[C.ids[t]];
-          FockPlan* plan = nullptr;
-          FSIM_TRY(get_plan(b, bt->tau, 0, 1, prec == 0 ? FSIM_FP64 : FSIM_MIXED, &plan, 1));
-          const ClassPairPlan& cp = plan->cp[X][Y];
-          CoopParams<Real> p{};
-          p.bra = b->cls[X].view<Real>();
-          p.ket = b->cls[Y].view<Real>();
-          make_cls_desc(X, p.bd);
-          make_cls_desc(Y, p.kd);
-          p.same = X == Y ? 1 : 0;
-          p.tile_prefix = cp.d_prefix;
-          p.ket_count = cp.d_count;
-          p.tq = cp.tq;
-          p.nitems = cp.nitems;
-          p.N = b->nbf;
-          p.D = mixed ? (const Real*)bt->h_ptrs[C.ids[t]].D32 : (const Real*)bt->h_ptrs[C.ids[t]].Din;
-          p.J = b->d_Jacc;
-          p.K = b->d_Kacc;
-          p.boys = std::is_same<Real, double>::value ? (const Real*)b->d_boys64 : (const Real*)b->d_boys32;
-          p.boys64_T = INFINITY;
-          e = launch_coop<Real>(p, cp.nitems, s);
-        }
-      } else {
+      {
         JKParams<Real> p{};
         p.mols = (const JKMol<Real>*)C.d_mols;
         p.mol_prefix = C.d_prefix;

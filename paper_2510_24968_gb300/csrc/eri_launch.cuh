@@ -16,6 +16,8 @@ cudaError_t launch_jk(const JKParams<Real>& p, cudaStream_t s) {
   constexpr int LA = pair_cls_la(X), LB = pair_cls_lb(X), LC = pair_cls_la(Y), LD = pair_cls_lb(Y);
   constexpr int CS = chunk_size<Real>(X, Y);
   using BC = PairCls<LA, LB>;
+  static_assert((size_t)(CS + 1) * BC::NC * kJKThreads * sizeof(Real) <= kJKBlockSmemMax,
+                "per-thread quartet blocks exceed the shared-memory budget");
   auto k = jk_kernel<Real, LA, LB, LC, LD, CS>;
   const size_t smem = (jk_boys_smem<Real>() + 15) / 16 * 16 + (1 + kJKThreads / 32) * BC::NC * sizeof(Real) +
                       (size_t)(CS + 1) * BC::NC * kJKThreads * sizeof(Real) +

@@ -31,40 +31,30 @@ int device_sm_count() {
   return n;
 }
 
-template <typename Real, int X, int Y>
-static cudaError_t launch_jk_if(const JKParams<Real>& p, cudaStream_t s) {
-  constexpr int L = pair_cls_la(X) + pair_cls_lb(X) + pair_cls_la(Y) + pair_cls_lb(Y);
-  if constexpr (std::is_same<Real, double>::value && L >= kCoopMinL64) {
-    return cudaErrorInvalidValue;  // these run on the cooperative kernel
-  } else {
-    return launch_jk<Real, X, Y>(p, s);
-  }
-}
-
 template <typename Real>
 static cudaError_t dispatch_jk(int X, int Y, const JKParams<Real>& p, cudaStream_t s) {
   switch (X * 8 + Y) {
-    case 0: return launch_jk_if<Real, 0, 0>(p, s);
-    case 8: return launch_jk_if<Real, 1, 0>(p, s);
-    case 9: return launch_jk_if<Real, 1, 1>(p, s);
-    case 16: return launch_jk_if<Real, 2, 0>(p, s);
-    case 17: return launch_jk_if<Real, 2, 1>(p, s);
-    case 18: return launch_jk_if<Real, 2, 2>(p, s);
-    case 24: return launch_jk_if<Real, 3, 0>(p, s);
-    case 25: return launch_jk_if<Real, 3, 1>(p, s);
-    case 26: return launch_jk_if<Real, 3, 2>(p, s);
-    case 27: return launch_jk_if<Real, 3, 3>(p, s);
-    case 32: return launch_jk_if<Real, 4, 0>(p, s);
-    case 33: return launch_jk_if<Real, 4, 1>(p, s);
-    case 34: return launch_jk_if<Real, 4, 2>(p, s);
-    case 35: return launch_jk_if<Real, 4, 3>(p, s);
-    case 36: return launch_jk_if<Real, 4, 4>(p, s);
-    case 40: return launch_jk_if<Real, 5, 0>(p, s);
-    case 41: return launch_jk_if<Real, 5, 1>(p, s);
-    case 42: return launch_jk_if<Real, 5, 2>(p, s);
-    case 43: return launch_jk_if<Real, 5, 3>(p, s);
-    case 44: return launch_jk_if<Real, 5, 4>(p, s);
-    case 45: return launch_jk_if<Real, 5, 5>(p, s);
+    case 0: return launch_jk<Real, 0, 0>(p, s);
+    case 8: return launch_jk<Real, 1, 0>(p, s);
+    case 9: return launch_jk<Real, 1, 1>(p, s);
+    case 16: return launch_jk<Real, 2, 0>(p, s);
+    case 17: return launch_jk<Real, 2, 1>(p, s);
+    case 18: return launch_jk<Real, 2, 2>(p, s);
+    case 24: return launch_jk<Real, 3, 0>(p, s);
+    case 25: return launch_jk<Real, 3, 1>(p, s);
+    case 26: return launch_jk<Real, 3, 2>(p, s);
+    case 27: return launch_jk<Real, 3, 3>(p, s);
+    case 32: return launch_jk<Real, 4, 0>(p, s);
+    case 33: return launch_jk<Real, 4, 1>(p, s);
+    case 34: return launch_jk<Real, 4, 2>(p, s);
+    case 35: return launch_jk<Real, 4, 3>(p, s);
+    case 36: return launch_jk<Real, 4, 4>(p, s);
+    case 40: return launch_jk<Real, 5, 0>(p, s);
+    case 41: return launch_jk<Real, 5, 1>(p, s);
+    case 42: return launch_jk<Real, 5, 2>(p, s);
+    case 43: return launch_jk<Real, 5, 3>(p, s);
+    case 44: return launch_jk<Real, 5, 4>(p, s);
+    case 45: return launch_jk<Real, 5, 5>(p, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -180,10 +170,9 @@ int get_plan(fsim_basis* b, double tau, int shard, int nshards, int precision, F
       if (CX.n == 0 || b->cls[Y].n == 0) continue;
       std::vector<int> count;
       cp.nquartets = screened_counts(b, X, Y, tau, shard, nshards, count);
-      const int L = pair_cls_la(X) + pair_cls_lb(X) + pair_cls_la(Y) + pair_cls_lb(Y);
-      const int coop = (precision == FSIM_FP64 && L >= kCoopMinL64) ? 1 : 0;
+      const int coop = 0;  // the cooperative kernel is an autotuner candidate only
       int ps = 1, cs = 1;
-      if (!coop) {
+      {
         if (psplit_force > 0) {
           ps = std::min(psplit_force, CX.ppmax);
         } else {
@@ -703,17 +692,14 @@ static int autotune_impl(fsim_basis* b, FockPlan* plan, const Real* Dr, float b6
       if (cp.nquartets == 0) continue;
       std::vector<int> count;
       screened_counts(b, X, Y, plan->tau, plan->shard, plan->nshards, count);
-      const int L = pair_cls_la(X) + pair_cls_lb(X) + pair_cls_la(Y) + pair_cls_lb(Y);
       struct Cand {
         int psplit, coop, csplit;
       };
       std::vector<Cand> cands;
-      const bool unrolled_ok = !(std::is_same<Real, double>::value && L >= kCoopMinL64);
       const int nch = jk_chunks<Real>(X, Y);
-      if (unrolled_ok)
-        for (int ps : {1, 3, 9})
-          for (int cs : {1, 2, 4})
-            if (ps <= b->cls[X].ppmax && cs <= nch) cands.push_back({ps, 0, cs});
+      for (int ps : {1, 3, 9})
+        for (int cs : {1, 2, 4})
+          if (ps <= b->cls[X].ppmax && cs <= nch) cands.push_back({ps, 0, cs});
       cands.push_back({1, 1, 1});
       float best = 1e30f;
       Cand win = cands[0];

@@ -81,16 +81,23 @@ inline PairView<float> DevClass::view<float>() const {
 // Ket components per register chunk.  The per-thread registers of the unrolled
 // kernel hold R (nherm(L)), the chunk's W (bra Hermite terms x CS) and the
 // chunk's E non-zeros; the quartet block itself lives in shared memory.  The
-// largest chunk whose estimate fits kChunkRegBudget is taken (the last chunk
-// may be shorter).
-// FP64 kernels keep the whole quartet in one chunk: GB300 issues FP64 FMAs at a
-// small fraction of the FP32 rate, so arrays that overflow into L1-resident
-// local memory do not limit them, while chunking would repeat the Hermite
-// recursion per chunk.
+// largest chunk whose estimate fits the budget is taken (the last chunk may be
+// shorter; chunks are balanced).
+// FP64 classes with L <= 4 keep the whole quartet in one chunk: GB300 issues
+// FP64 FMAs at a small fraction of the FP32 rate, so arrays that overflow into
+// L1-resident local memory cost little, while every extra chunk repeats the
+// Boys function and the Hermite recursion on the FP64 pipe.  From L = 5 on the
+// FP64 quartet no longer fits and is chunked with its own (smaller) budget.
 #ifndef FSIM_CHUNK_REG_BUDGET
 #define FSIM_CHUNK_REG_BUDGET 170
 #endif
+#ifndef FSIM_CHUNK_REG_BUDGET64
+#define FSIM_CHUNK_REG_BUDGET64 120
+#endif
 constexpr int kChunkRegBudget = FSIM_CHUNK_REG_BUDGET;
+// shared memory for the per-thread quartet blocks and J_bra partials of a CTA
+constexpr size_t kJKBlockSmemMax = 160 * 1024;
+constexpr int kChunkRegBudget64 = FSIM_CHUNK_REG_BUDGET64;
 
 __host__ __device__ constexpr int pair_comp_nnz(int la, int lb, int c) {
   int p = 1;
@@ -113,11 +120,14 @@ template <typename Real>
 __host__ __device__ constexpr int chunk_size(int X, int Y) {
   const int lc = pair_cls_la(Y), ld = pair_cls_lb(Y);
   const int C = ncart(lc) * ncart(ld);
-  if (sizeof(Real) == 8) return C;
+  if (sizeof(Real) == 8 && pair_cls_la(X) + pair_cls_lb(X) + lc + ld <= 4) return C;
+  const int budget = sizeof(Real) == 8 ? kChunkRegBudget64 : kChunkRegBudget;
   const int H1 = nherm(pair_cls_la(X) + pair_cls_lb(X));
   const int NH = nherm(pair_cls_la(X) + pair_cls_lb(X) + lc + ld);
+  const int A = ncart(pair_cls_la(X)) * ncart(pair_cls_lb(X));
   for (int cs = C; cs > 1; --cs)
-    if (NH + H1 * cs + chunk_nnz_max(lc, ld, cs) <= kChunkRegBudget) {
+    if (NH + H1 * cs + chunk_nnz_max(lc, ld, cs) <= budget &&
+        (size_t)(cs + 1) * A * kJKThreads * sizeof(Real) <= kJKBlockSmemMax) {
       const int nch = (C + cs - 1) / cs;
       return (C + nch - 1) / nch;  // same chunk count, balanced sizes
     }
@@ -160,8 +170,7 @@ template <typename Real>
 struct CoopParams;
 template <typename Real>
 cudaError_t launch_coop(const CoopParams<Real>& p, int nblocks, cudaStream_t s);
-// FP64 classes with L = la+lb+lc+ld >= this run on the cooperative kernel
-constexpr int kCoopMinL64 = 5;
+
 
 }  // namespace fsim
 

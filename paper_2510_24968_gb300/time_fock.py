@@ -57,6 +57,7 @@ def main(argv=None):
         gb.fock_build(D, J, K, **kw)
         torch.cuda.synchronize()
         ts = []
+        torch.cuda.nvtx.range_push(f"time_fock_{name}")  # profilers can filter on this range
         for _ in range(a.reps):
             s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             s.record()
@@ -64,6 +65,7 @@ def main(argv=None):
             e.record()
             torch.cuda.synchronize()
             ts.append(s.elapsed_time(e))
+        torch.cuda.nvtx.range_pop()
         q = gb.last_quartet_count()
         gb.fock_build(D, J, K, timing=True, **kw)
         ms, qs, nl = gb.last_class_times()
