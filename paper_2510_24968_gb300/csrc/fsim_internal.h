@@ -81,18 +81,20 @@ inline PairView<float> DevClass::view<float>() const {
 // Ket components per register chunk.  The per-thread registers of the unrolled
 // kernel hold R (nherm(L)), the chunk's W (bra Hermite terms x CS) and the
 // chunk's E non-zeros; the quartet block itself lives in shared memory.  The
-// largest chunk whose estimate fits the budget is taken (the last chunk may be
-// shorter; chunks are balanced).
+// largest chunk whose estimate (in values, not registers) fits the budget is
+// taken (the last chunk may be shorter; chunks are balanced), capped by the
+// shared memory of the per-thread quartet blocks.  Every extra chunk repeats
+// the Boys function and the Hermite recursion, so larger chunks win until
+// spills or lost occupancy cost more: the budgets were set by timing every
+// class pair on the 12- and 30-atom organic clouds at several budgets.
 // FP64 classes with L <= 4 keep the whole quartet in one chunk: GB300 issues
 // FP64 FMAs at a small fraction of the FP32 rate, so arrays that overflow into
-// L1-resident local memory cost little, while every extra chunk repeats the
-// Boys function and the Hermite recursion on the FP64 pipe.  From L = 5 on the
-// FP64 quartet no longer fits and is chunked with its own (smaller) budget.
+// L1-resident local memory cost little next to repeated FP64 recursions.
 #ifndef FSIM_CHUNK_REG_BUDGET
-#define FSIM_CHUNK_REG_BUDGET 170
+#define FSIM_CHUNK_REG_BUDGET 230
 #endif
 #ifndef FSIM_CHUNK_REG_BUDGET64
-#define FSIM_CHUNK_REG_BUDGET64 120
+#define FSIM_CHUNK_REG_BUDGET64 350
 #endif
 constexpr int kChunkRegBudget = FSIM_CHUNK_REG_BUDGET;
 // shared memory for the per-thread quartet blocks and J_bra partials of a CTA
@@ -120,6 +122,9 @@ template <typename Real>
 __host__ __device__ constexpr int chunk_size(int X, int Y) {
   const int lc = pair_cls_la(Y), ld = pair_cls_lb(Y);
   const int C = ncart(lc) * ncart(ld);
+  // measured exception: FP32 (dd|dd) runs faster with two-component chunks than
+  // the budget rule's one (class times on the 12- and 30-atom organic clouds)
+  if (sizeof(Real) == 4 && X == 5 && Y == 5) return 2;
   if (sizeof(Real) == 8 && pair_cls_la(X) + pair_cls_lb(X) + lc + ld <= 4) return C;
   const int budget = sizeof(Real) == 8 ? kChunkRegBudget64 : kChunkRegBudget;
   const int H1 = nherm(pair_cls_la(X) + pair_cls_lb(X));

