@@ -178,7 +178,7 @@ int fsim_last_class_times(fsim_basis* b, float* ms, long long* quartets, int* nl
 /*
  * Contracted ERI blocks (mu nu|la si) for explicit shell quartets (debug /
  * parity), by the FP64 warp-cooperative quartet kernel that also serves the
- * Schwarz diagonal and the FP64 Fock build of the classes with la+lb+lc+ld >= 5.
+ * Schwarz diagonal.
  * quartets: 4*n shell indices (a,b,c,d); out: concatenated blocks, each
  * na*nb*nc*nd in (a,b,c,d) row-major order; host pointers; precision must be
  * FSIM_FP64.
