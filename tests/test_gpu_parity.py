@@ -254,6 +254,22 @@ def test_scf_fp64_water(water_oracle_scf):
     assert np.abs(r["D"] - ro.D).max() < 1e-6
 
 
+@pytest.mark.parametrize("diis", [True, False])
+def test_scf_trajectory_water(diis):
+    # the SCF iteration itself (Sec. 3.2; DIIS per Algorithm 1, or plain), energy by
+    # energy against the oracle's: same guess, same extrapolation, same aufbau
+    from oracle import OracleBasis, rhf
+    from paper_2510_24968_gb300 import FSIM_FP64, Basis
+    mol = workload("water")
+    ob = OracleBasis(mol)
+    S, H = ob.onee("S"), ob.onee("T") + ob.onee("V")
+    ro = rhf(S, H, lambda D: ob.jk(D)[:2], mol.nelec, ob.enuc(), max_iter=40, diis=diis)
+    r = Basis(mol).scf(precision=FSIM_FP64, tau=0.0, max_iter=40, diis_size=8 if diis else 0)
+    n = min(len(ro.energies), len(r["energies"]))
+    assert n >= 8 and r["iters"] == ro.iters and r["converged"] == ro.converged
+    assert np.abs(np.array(ro.energies[:n]) - r["energies"][:n]).max() < 1e-9
+
+
 def test_scf_mixed_water(water_oracle_scf):
     # mixed builds with FP64 resets reach the FP64 energy; without the resets the
     # FP32 error of this near-linearly-dependent basis stays at the 1e-4 Eh level
