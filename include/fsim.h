@@ -73,8 +73,26 @@ typedef struct {
  */
 int fsim_basis_create(const fsim_atom* atoms, int natom, const fsim_shell_desc* shells, int nshell,
                       fsim_basis** out);
+
+/*
+ * The same with flags.  FSIM_BASIS_SPHERICAL: the basis the caller sees is the
+ * real solid-harmonic one of Sec. 2.1.1 (2l+1 functions per shell: s; p in x, y,
+ * z order; d as m = -2..2: xy, yz, z^2 - (x^2+y^2)/2, xz, (sqrt 3/2)(x^2 - y^2)
+ * on the unit-normalised Cartesian components, each unit-normalised).  The
+ * integrals are still evaluated over Cartesian shells; fsim_onee,
+ * fsim_fock_build and fsim_scf take and return matrices in the spherical basis
+ * (D_cart = T^T D T before the build, J = T J_cart T^T after).  fsim_eri_quartets
+ * and fsim_eri_dump stay Cartesian; batches, the learned guess and
+ * fsim_fock_build_noalloc reject spherical bases (FSIM_EINVAL).
+ */
+#define FSIM_BASIS_SPHERICAL 1
+int fsim_basis_create_ex(const fsim_atom* atoms, int natom, const fsim_shell_desc* shells, int nshell, int flags,
+                         fsim_basis** out);
 void fsim_basis_destroy(fsim_basis* b);
+/* Functions of the basis the caller sees (spherical count for spherical bases). */
 int fsim_basis_nbf(const fsim_basis* b);
+/* Cartesian functions of the integral engine (equal to fsim_basis_nbf for Cartesian bases). */
+int fsim_basis_nbf_cart(const fsim_basis* b);
 int fsim_basis_nshell(const fsim_basis* b);
 /* Number of unique shell pairs in each of the six pair classes ss, ps, pp, ds, dp, dd. */
 int fsim_basis_pair_counts(const fsim_basis* b, int counts[6]);

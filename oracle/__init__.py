@@ -7,6 +7,7 @@ shares no code with the CUDA library; both read the same seeded inputs from
 """
 from .oracle import (OracleBasis, build, boys, hermite_E, hermite_R, jacobi_eigh)
 from .scf import rhf, core_guess_density
+from .spherical import SphericalOracleBasis
 
 __all__ = ["OracleBasis", "build", "boys", "hermite_E", "hermite_R", "jacobi_eigh",
-           "rhf", "core_guess_density"]
+           "rhf", "core_guess_density", "SphericalOracleBasis"]

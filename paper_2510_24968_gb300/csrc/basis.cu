@@ -348,6 +348,16 @@ const char* fsim_last_error(void) { return fsim::last_error(); }
 
 int fsim_basis_create(const fsim_atom* atoms, int natom, const fsim_shell_desc* shells, int nshell,
                       fsim_basis** out) {
+  return fsim_basis_create_ex(atoms, natom, shells, nshell, 0, out);
+}
+
+int fsim_basis_create_ex(const fsim_atom* atoms, int natom, const fsim_shell_desc* shells, int nshell, int flags,
+                         fsim_basis** out) {
+  if (out) *out = nullptr;
+  if (flags & ~FSIM_BASIS_SPHERICAL) {
+    set_error("fsim_basis_create_ex: unknown flags %#x", flags);
+    return FSIM_EINVAL;
+  }
   if (!out || !atoms || !shells || natom <= 0 || nshell <= 0) {
     set_error("fsim_basis_create: null pointer or empty input");
     return FSIM_EINVAL;
@@ -445,6 +455,10 @@ int fsim_basis_create(const fsim_atom* atoms, int natom, const fsim_shell_desc* 
     }
   for (int X = 0; X < kNumPairCls; ++X)
     if ((rc = build_pair_data(b, X, order[X])) != FSIM_OK) return fail(rc);
+  if (flags & FSIM_BASIS_SPHERICAL) {
+    b->spherical = 1;
+    if ((rc = sph_setup(b)) != FSIM_OK) return fail(rc);
+  }
   if (cudaDeviceSynchronize() != cudaSuccess) {
     set_error("fsim_basis_create: %s", cudaGetErrorString(cudaGetLastError()));
     return fail(FSIM_ECUDA);
@@ -471,6 +485,8 @@ void fsim_basis_destroy(fsim_basis* b) {
   dev_free(b->d_boys64); dev_free(b->d_boys32);
   dev_free(b->d_Jacc); dev_free(b->d_Kacc); dev_free(b->d_D); dev_free(b->d_J); dev_free(b->d_K);
   dev_free(b->d_D32);
+  dev_free(b->d_sti); dev_free(b->d_stc); dev_free(b->d_sci); dev_free(b->d_scc);
+  dev_free(b->d_cD); dev_free(b->d_cJ); dev_free(b->d_cK);
   if (b->ev_ok)
     for (auto& pr : b->ev)
       for (auto& e : pr) cudaEventDestroy(e);
@@ -484,7 +500,8 @@ void fsim_basis_destroy(fsim_basis* b) {
   delete b;
 }
 
-int fsim_basis_nbf(const fsim_basis* b) { return b ? b->nbf : FSIM_EINVAL; }
+int fsim_basis_nbf(const fsim_basis* b) { return b ? b->nbf_ext() : FSIM_EINVAL; }
+int fsim_basis_nbf_cart(const fsim_basis* b) { return b ? b->nbf : FSIM_EINVAL; }
 int fsim_basis_nshell(const fsim_basis* b) { return b ? b->nshell : FSIM_EINVAL; }
 
 int fsim_basis_pair_counts(const fsim_basis* b, int counts[6]) {
@@ -518,11 +535,11 @@ int fsim_onee(fsim_basis* b, int which, double* out, int ptr_mode, void* stream)
     return FSIM_EINVAL;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t n2 = (size_t)b->nbf * b->nbf;
-  if (ptr_mode == FSIM_PTR_DEVICE) return onee_device(b, which, out, s);
+  const size_t n2 = (size_t)b->nbf_ext() * b->nbf_ext();
+  if (ptr_mode == FSIM_PTR_DEVICE) return onee_ext_device(b, which, out, s);
   double* d = nullptr;
   FSIM_TRY(dev_alloc(&d, n2));
-  int rc = onee_device(b, which, d, s);
+  int rc = onee_ext_device(b, which, d, s);
   if (rc == FSIM_OK) {
     if (cudaMemcpyAsync(out, d, n2 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {

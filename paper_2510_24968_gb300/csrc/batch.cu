@@ -211,6 +211,11 @@ int fsim_batch_create(fsim_basis* const* bases, int nmol, const fsim_fock_opts* 
     set_error("fsim_batch_create: bad arguments");
     return FSIM_EINVAL;
   }
+  for (int m = 0; m < nmol; ++m)
+    if (!bases[m] || bases[m]->spherical) {
+      set_error("fsim_batch_create: molecule %d: null or spherical basis (batches are Cartesian)", m);
+      return FSIM_EINVAL;
+    }
   *out = nullptr;
   fsim_batch* bt = new fsim_batch();
   bt->nmol = nmol;
@@ -465,8 +470,8 @@ extern "C" int fsim_scf_batched(fsim_basis* const* bases, int nmol, const fsim_s
   for (int i = 0; i < nmol; ++i) {
     Mol& m = mols[i];
     m.b = bases[i];
-    if (!m.b) {
-      set_error("fsim_scf_batched: null basis %d", i);
+    if (!m.b || m.b->spherical) {
+      set_error("fsim_scf_batched: basis %d is null or spherical (batches are Cartesian)", i);
       return FSIM_EINVAL;
     }
     m.N = m.b->nbf;

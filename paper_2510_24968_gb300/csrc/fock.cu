@@ -450,18 +450,18 @@ int fsim_fock_build(fsim_basis* b, const double* D, double* J, double* K, const 
   fsim_fock_opts o;
   fsim_fock_opts_default(&o);
   if (opts) o = *opts;
-  if (o.ptr_mode == FSIM_PTR_DEVICE) return fock_build_device(b, D, J, K, o);
+  if (o.ptr_mode == FSIM_PTR_DEVICE) return fock_build_ext_device(b, D, J, K, o);
   if (o.ptr_mode != FSIM_PTR_HOST) {
     set_error("fsim_fock_build: bad ptr_mode");
     return FSIM_EINVAL;
   }
-  const size_t n2 = (size_t)b->nbf * b->nbf;
+  const size_t n2 = (size_t)b->nbf_ext() * b->nbf_ext();
   cudaStream_t s = (cudaStream_t)o.stream;
-  if (!b->d_D) FSIM_TRY(dev_alloc(&b->d_D, n2));
-  if (!b->d_J) FSIM_TRY(dev_alloc(&b->d_J, n2));
-  if (!b->d_K) FSIM_TRY(dev_alloc(&b->d_K, n2));
+  if (!b->d_D) FSIM_TRY(dev_alloc(&b->d_D, (size_t)b->nbf * b->nbf));
+  if (!b->d_J) FSIM_TRY(dev_alloc(&b->d_J, (size_t)b->nbf * b->nbf));
+  if (!b->d_K) FSIM_TRY(dev_alloc(&b->d_K, (size_t)b->nbf * b->nbf));
   FSIM_CK(cudaMemcpyAsync(b->d_D, D, n2 * sizeof(double), cudaMemcpyHostToDevice, s));
-  FSIM_TRY(fock_build_device(b, b->d_D, b->d_J, b->d_K, o));
+  FSIM_TRY(fock_build_ext_device(b, b->d_D, b->d_J, b->d_K, o));
   FSIM_CK(cudaMemcpyAsync(J, b->d_J, n2 * sizeof(double), cudaMemcpyDeviceToHost, s));
   FSIM_CK(cudaMemcpyAsync(K, b->d_K, n2 * sizeof(double), cudaMemcpyDeviceToHost, s));
   FSIM_CK(cudaStreamSynchronize(s));

@@ -181,7 +181,18 @@ cudaError_t launch_coop(const CoopParams<Real>& p, int nblocks, cudaStream_t s);
 
 struct fsim_basis {
   int device = 0;
-  int natom = 0, nshell = 0, nbf = 0;
+  int natom = 0, nshell = 0, nbf = 0;  // nbf: Cartesian functions (the integral engine's basis)
+  // spherical (real solid-harmonic) basis on top of the Cartesian engine: nsph
+  // functions, T rows (index, coef) x 3 and T columns (index, coef) x 2
+  int spherical = 0, nsph = 0;
+  int* d_sti = nullptr;
+  double* d_stc = nullptr;
+  int* d_sci = nullptr;
+  double* d_scc = nullptr;
+  double* d_cD = nullptr;  // Cartesian D, J, K of a spherical build
+  double* d_cJ = nullptr;
+  double* d_cK = nullptr;
+  int nbf_ext() const { return spherical ? nsph : nbf; }
   std::vector<int> Z;
   std::vector<double> axyz;
   std::vector<int> sh_atom, sh_l, sh_nprim, sh_ao;
@@ -236,5 +247,9 @@ int build_pair_data(fsim_basis* b, int cls, const std::vector<int4>& order);
 int run_list(fsim_basis* b, int X, int Y, const std::vector<int2>& items, double* d_out, int precision,
              cudaStream_t s);
 int fock_build_device(fsim_basis* b, const double* dD, double* dJ, double* dK, const fsim_fock_opts& o);
+// the same in the basis the caller sees (spherical when the basis is)
+int fock_build_ext_device(fsim_basis* b, const double* dD, double* dJ, double* dK, const fsim_fock_opts& o);
+int onee_ext_device(fsim_basis* b, int which, double* out, cudaStream_t s);
+int sph_setup(fsim_basis* b);
 int onee_device(fsim_basis* b, int which, double* d_out, cudaStream_t s);
 }  // namespace fsim

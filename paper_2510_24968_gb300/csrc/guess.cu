@@ -300,6 +300,10 @@ int fsim_guess_layout(const fsim_basis* b, int* npairs, int* nfeat, int* nout) {
     set_error("fsim_guess_layout: null pointer");
     return FSIM_EINVAL;
   }
+  if (b->spherical) {
+    set_error("fsim_guess_layout: the learned guess works on Cartesian bases only");
+    return FSIM_EINVAL;
+  }
   std::vector<AtomFns> at;
   FSIM_TRY(atom_layout(b, at));
   *npairs = b->natom * (b->natom + 1) / 2;
@@ -313,6 +317,10 @@ int fsim_guess_features(const fsim_basis* b, float* feat) {
     set_error("fsim_guess_features: null pointer");
     return FSIM_EINVAL;
   }
+  if (b->spherical) {
+    set_error("fsim_guess_features: the learned guess works on Cartesian bases only");
+    return FSIM_EINVAL;
+  }
   std::vector<AtomFns> at;
   FSIM_TRY(atom_layout(b, at));
   std::vector<PairGeo> pg;
@@ -324,6 +332,10 @@ int fsim_guess_features(const fsim_basis* b, float* feat) {
 int fsim_guess_targets(const fsim_basis* b, const double* D, float* target, float* mask) {
   if (!b || !D || !target || !mask) {
     set_error("fsim_guess_targets: null pointer");
+    return FSIM_EINVAL;
+  }
+  if (b->spherical) {
+    set_error("fsim_guess_targets: the learned guess works on Cartesian bases only");
     return FSIM_EINVAL;
   }
   std::vector<AtomFns> at;
@@ -364,6 +376,10 @@ int fsim_guess_targets(const fsim_basis* b, const double* D, float* target, floa
 int fsim_guess_assemble(fsim_basis* b, const float* blocks, double* D, void* stream) {
   if (!b || !blocks || !D) {
     set_error("fsim_guess_assemble: null pointer");
+    return FSIM_EINVAL;
+  }
+  if (b->spherical) {
+    set_error("fsim_guess_assemble: the learned guess works on Cartesian bases only");
     return FSIM_EINVAL;
   }
   std::vector<AtomFns> at;

@@ -81,6 +81,10 @@ extern "C" int fsim_fock_build_noalloc(fsim_basis* b, const double* D, double* J
     fsim::set_error("fsim_fock_build_noalloc: per-kernel timing is not available here (it creates CUDA events)");
     return FSIM_EINVAL;
   }
+  if (b->spherical) {
+    fsim::set_error("fsim_fock_build_noalloc: spherical bases are not supported (use fsim_fock_build)");
+    return FSIM_EINVAL;
+  }
   if (b->nbf > kNoAllocMaxN) {
     fsim::set_error("fsim_fock_build_noalloc: %d basis functions exceed the fixed scratch capacity of %d", b->nbf,
                     kNoAllocMaxN);

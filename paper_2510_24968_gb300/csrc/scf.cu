@@ -232,7 +232,7 @@ int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res) {
     return FSIM_EINVAL;
   }
   const fsim_scf_opts& o = *opts;
-  const int N = b->nbf;
+  const int N = b->nbf_ext();
   if (o.nelec <= 0 || (o.nelec & 1) || o.nelec / 2 > N || o.max_iter < 1 || o.diis_size < 0 ||
       (o.guess == FSIM_GUESS_DENSITY && !o.D0) || (o.guess != FSIM_GUESS_CORE && o.guess != FSIM_GUESS_DENSITY)) {
     set_error("fsim_scf: bad options (nelec %d must be even and <= 2 nbf, max_iter %d)", o.nelec, o.max_iter);
@@ -277,9 +277,9 @@ int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res) {
   int rc = FSIM_OK;
 
   // one-electron matrices and H = T + V
-  FSIM_TRY(onee_device(b, 0, S, c.s));
-  FSIM_TRY(onee_device(b, 1, T, c.s));
-  FSIM_TRY(onee_device(b, 2, tmp, c.s));
+  FSIM_TRY(onee_ext_device(b, 0, S, c.s));
+  FSIM_TRY(onee_ext_device(b, 1, T, c.s));
+  FSIM_TRY(onee_ext_device(b, 2, tmp, c.s));
   add_kernel<<<bl, th, 0, c.s>>>(T, tmp, 1.0, H, n2);
   FSIM_CK(cudaGetLastError());
   // X = U s^{-1/2} U^T
@@ -369,11 +369,11 @@ int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res) {
     fo.precision = want64 ? FSIM_FP64 : FSIM_MIXED;
     if (o.incremental && have_G && !want64) {
       add_kernel<<<bl, th, 0, c.s>>>(D, Dn, -1.0, dD, n2);  // dD = D - D_prev (Dn holds D_prev)
-      FSIM_TRY(fock_build_device(b, dD, J, K, fo));
+      FSIM_TRY(fock_build_ext_device(b, dD, J, K, fo));
       add_kernel<<<bl, th, 0, c.s>>>(G, J, 1.0, G, n2);
       add_kernel<<<bl, th, 0, c.s>>>(G, K, -0.5, G, n2);
     } else {
-      FSIM_TRY(fock_build_device(b, D, J, K, fo));
+      FSIM_TRY(fock_build_ext_device(b, D, J, K, fo));
       add_kernel<<<bl, th, 0, c.s>>>(J, K, -0.5, G, n2);
       have_G = true;
       if (mixed && want64) {

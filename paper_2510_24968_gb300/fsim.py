@@ -24,13 +24,15 @@ FSIM_EDEVICE_TIMEOUT = -5
 FSIM_ENOMEM = -6
 FSIM_FP64 = 0
 FSIM_MIXED = 1
+FSIM_BASIS_SPHERICAL = 1
 FSIM_PTR_HOST = 0
 FSIM_PTR_DEVICE = 1
 FSIM_GUESS_CORE = 0
 FSIM_GUESS_DENSITY = 1
 
 # every symbol declared in include/fsim.h
-EXPORTS = ["fsim_basis_create", "fsim_basis_destroy", "fsim_basis_nbf", "fsim_basis_nshell",
+EXPORTS = ["fsim_basis_create", "fsim_basis_create_ex", "fsim_basis_destroy", "fsim_basis_nbf",
+           "fsim_basis_nbf_cart", "fsim_basis_nshell",
            "fsim_basis_pair_counts", "fsim_enuc", "fsim_onee", "fsim_schwarz", "fsim_fock_opts_default",
            "fsim_fock_build", "fsim_fock_build_noalloc", "fsim_autotune", "fsim_last_quartet_count", "fsim_last_class_times", "fsim_eri_quartets", "fsim_eri_dump",
            "fsim_scf_opts_default", "fsim_scf", "fsim_batch_create", "fsim_batch_fock", "fsim_batch_destroy",
@@ -88,6 +90,9 @@ def load():
     dp, ip, vp = C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_void_p
     L.fsim_basis_create.argtypes = [C.POINTER(fsim_atom), C.c_int, C.POINTER(fsim_shell_desc), C.c_int,
                                     C.POINTER(vp)]
+    L.fsim_basis_create_ex.argtypes = [C.POINTER(fsim_atom), C.c_int, C.POINTER(fsim_shell_desc), C.c_int, C.c_int,
+                                       C.POINTER(C.c_void_p)]
+    L.fsim_basis_nbf_cart.argtypes = [vp]
     L.fsim_basis_destroy.argtypes = [vp]
     L.fsim_basis_destroy.restype = None
     L.fsim_basis_nbf.argtypes = [vp]
@@ -169,7 +174,7 @@ def fsim_scf_opts_default() -> fsim_scf_opts:
 class Basis:
     """Owns an fsim_basis handle built from a fsim_synth.Molecule."""
 
-    def __init__(self, mol):
+    def __init__(self, mol, spherical=False):
         L = load()
         a = mol.arrays()
         atoms = (fsim_atom * mol.natom)()
@@ -186,10 +191,13 @@ class Basis:
             shells[s].atom, shells[s].l, shells[s].nprim = sh.atom, sh.l, len(sh.alpha)
             shells[s].alpha, shells[s].coef = _dptr(al), _dptr(co)
         h = C.c_void_p()
-        _check(L.fsim_basis_create(atoms, mol.natom, shells, mol.nshell, C.byref(h)))
+        _check(L.fsim_basis_create_ex(atoms, mol.natom, shells, mol.nshell, FSIM_BASIS_SPHERICAL if spherical else 0,
+                                      C.byref(h)))
         self.h = h
         self.mol = mol
+        self.spherical = bool(spherical)
         self.nbf = L.fsim_basis_nbf(h)
+        self.nbf_cart = L.fsim_basis_nbf_cart(h)
         self.nshell = L.fsim_basis_nshell(h)
 
     def close(self):
@@ -282,7 +290,8 @@ class Basis:
         return blocks
 
     def eri_dump(self) -> np.ndarray:
-        N = self.nbf
+        """All Cartesian ERIs (nbf_cart^4), also for spherical bases."""
+        N = self.nbf_cart
         g = np.zeros(N ** 4)
         _check(load().fsim_eri_dump(self.h, _dptr(g), FSIM_FP64))
         return g.reshape(N, N, N, N)

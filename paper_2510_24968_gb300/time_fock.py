@@ -34,14 +34,16 @@ def main(argv=None):
     ap.add_argument("--tune", action="store_true", help="autotune launch shapes first")
     ap.add_argument("--boys-fp64-T", type=float, default=0.0)
     ap.add_argument("--scf", action="store_true", help="also run the SCF to convergence")
+    ap.add_argument("--spherical", action="store_true", help="real solid-harmonic basis")
     a = ap.parse_args(argv)
 
     mol = workload(a.workload)
     t0 = time.perf_counter()
-    gb = Basis(mol)
+    gb = Basis(mol, spherical=a.spherical)
     gb.schwarz()
     torch.cuda.synchronize()
-    out = {"workload": a.workload, "nbf": gb.nbf, "nshell": mol.nshell, "tau": a.tau,
+    out = {"workload": a.workload, "nbf": gb.nbf, "nbf_cart": gb.nbf_cart, "spherical": a.spherical,
+           "nshell": mol.nshell, "tau": a.tau,
            "setup_s": time.perf_counter() - t0}
     N = gb.nbf
     Dn = np.random.default_rng(0).standard_normal((N, N)) * 0.02

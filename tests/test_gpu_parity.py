@@ -270,6 +270,52 @@ def test_scf_trajectory_water(diis):
     assert np.abs(np.array(ro.energies[:n]) - r["energies"][:n]).max() < 1e-9
 
 
+# ------------------------------------------------------------------ spherical basis
+def test_spherical_onee_jk_match_oracle():
+    # (H2O)_2 with O d shells in the real solid-harmonic basis: S, T, V and J, K of a
+    # spherical density against the oracle's own spherical transform
+    from oracle import SphericalOracleBasis
+    from paper_2510_24968_gb300 import FSIM_FP64, FSIM_MIXED, Basis
+    mol = workload("water2")
+    gb, ob = Basis(mol, spherical=True), SphericalOracleBasis(mol)
+    assert gb.nbf == ob.nbf and gb.nbf_cart == ob.nbf_cart and gb.nbf < gb.nbf_cart
+    for w in "STV":
+        assert np.abs(gb.onee(w) - ob.onee(w)).max() < 1e-11, w
+    D = _rand_sym(gb.nbf, 14) * 0.1
+    Jo, Ko, _ = ob.jk(D, tau=1e-10)
+    J, K = gb.fock_build(D, tau=1e-10, precision=FSIM_FP64)
+    assert np.abs(J - Jo).max() < 1e-10 and np.abs(K - Ko).max() < 1e-10
+    Jm, Km = gb.fock_build(D, tau=1e-10, precision=FSIM_MIXED)
+    s = np.abs(Jo).max()
+    assert np.abs(Jm - Jo).max() < 2e-6 * s and np.abs(Km - Ko).max() < 2e-6 * s
+
+
+def test_spherical_scf_energy_matches_oracle():
+    from oracle import SphericalOracleBasis, rhf
+    from paper_2510_24968_gb300 import FSIM_FP64, FSIM_MIXED, Basis
+    mol = workload("water2")
+    ob = SphericalOracleBasis(mol)
+    S, H = ob.onee("S"), ob.onee("T") + ob.onee("V")
+    ro = rhf(S, H, lambda D: ob.jk(D, tau=1e-10)[:2], mol.nelec, ob.enuc())
+    gb = Basis(mol, spherical=True)
+    for prec in (FSIM_FP64, FSIM_MIXED):
+        r = gb.scf(precision=prec, tau=1e-10)
+        assert r["converged"] and abs(r["e_total"] - ro.e_total) < 1e-8, prec
+    # the Cartesian energy of the same molecule lies below (larger variational space)
+    rc = Basis(mol).scf(precision=FSIM_FP64, tau=1e-10)
+    assert rc["e_total"] < ro.e_total - 1e-6
+
+
+def test_spherical_rejected_where_cartesian_only():
+    from paper_2510_24968_gb300 import FSIM_MIXED, Basis, FsimError, scf_batched
+    from paper_2510_24968_gb300 import guess
+    gb = Basis(workload("water"), spherical=True)
+    with pytest.raises(FsimError):
+        scf_batched([gb], precision=FSIM_MIXED, tau=1e-10, max_iter=2)
+    with pytest.raises(FsimError):
+        guess.features(gb)
+
+
 def test_scf_mixed_water(water_oracle_scf):
     # mixed builds with FP64 resets reach the FP64 energy; without the resets the
     # FP32 error of this near-linearly-dependent basis stays at the 1e-4 Eh level

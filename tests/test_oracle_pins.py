@@ -459,6 +459,71 @@ def test_scf_rotation_invariance(water_scf):
     assert r2.e_total == pytest.approx(r.e_total, abs=1e-9)
 
 
+# ---------------------------------------------------------------- spherical (real solid-harmonic) basis
+def _sph_scf(mol):
+    from oracle import SphericalOracleBasis
+    B = SphericalOracleBasis(mol)
+    S, H = B.onee("S"), B.onee("T") + B.onee("V")
+    return B, rhf(S, H, lambda D: B.jk(D)[:2], mol.nelec, B.enuc())
+
+
+def test_spherical_d_shell_orthonormal_and_free_of_r2():
+    # the five d functions of a shell are orthonormal (only their norms are imposed),
+    # and none overlaps an s shell on the same atom, while Cartesian xx does
+    from fsim_synth import water_cluster
+    from oracle import SphericalOracleBasis
+    mol = water_cluster(1, geom_seed=3)
+    B = SphericalOracleBasis(mol)
+    assert B.nbf == B.nbf_cart - sum(1 for s in mol.shells if s.l == 2)
+    S = B.onee("S")
+    Sc = B.cart.onee("S")
+    off = 0
+    for s in mol.shells:
+        n = 2 * s.l + 1
+        if s.l == 2:
+            assert np.abs(S[off:off + n, off:off + n] - np.eye(5)).max() < 1e-13
+            d_rows = range(off, off + n)
+            for t, u in enumerate(mol.shells):
+                if u.l == 0 and u.atom == s.atom:
+                    o = sum(2 * v.l + 1 for v in mol.shells[:t])
+                    assert max(abs(S[o, r]) for r in d_rows) < 1e-13
+                    oc = int(B.cart.ao[t])
+                    assert abs(Sc[oc, int(B.cart.ao[mol.shells.index(s)])]) > 0.05  # <s|xx> != 0
+        off += n
+
+
+def test_spherical_equals_cartesian_without_d():
+    from oracle import OracleBasis, SphericalOracleBasis
+    from fsim_synth import workload
+    mol = workload("water")
+    Bs, Bc = SphericalOracleBasis(mol), OracleBasis(mol)
+    assert Bs.nbf == Bc.nbf
+    for w in "STV":
+        assert np.abs(Bs.onee(w) - Bc.onee(w)).max() < 1e-14
+
+
+def test_spherical_energy_variational_and_rotation_invariant():
+    # the spherical space is a subspace of the Cartesian one (E_sph >= E_cart), and a
+    # rotation-invariant one: the energy of the rotated molecule is unchanged (a wrong
+    # d combination would span a subspace that rotates differently)
+    from fsim_synth import water_cluster
+    from oracle import OracleBasis
+    mol = water_cluster(1, geom_seed=3)
+    Bc = OracleBasis(mol)
+    Sc, Hc = Bc.onee("S"), Bc.onee("T") + Bc.onee("V")
+    rc = rhf(Sc, Hc, lambda D: Bc.jk(D)[:2], mol.nelec, Bc.enuc())
+    _, rs = _sph_scf(mol)
+    assert rs.converged and rc.converged
+    assert rs.e_total > rc.e_total + 1e-6
+    th = 0.7
+    Rm = np.array([[1.0, 0, 0], [0, math.cos(th), -math.sin(th)], [0, math.sin(th), math.cos(th)]])
+    Rm = Rm @ np.array([[math.cos(1.9), 0, math.sin(1.9)], [0, 1.0, 0], [-math.sin(1.9), 0, math.cos(1.9)]])
+    m2 = make_mol([(z, tuple(Rm @ x)) for z, x in zip(mol.Z, mol.xyz)],
+                  [(s.atom, s.l, s.alpha, s.coef) for s in mol.shells])
+    _, rs2 = _sph_scf(m2)
+    assert rs2.e_total == pytest.approx(rs.e_total, abs=1e-9)
+
+
 # ---------------------------------------------------------------- learned-guess network (FP64 reference)
 def test_mlp_oracle_gradient_finite_differences():
     from oracle import mlp
