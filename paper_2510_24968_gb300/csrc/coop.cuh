@@ -9,8 +9,8 @@
 //   * W[h][c] (ket transform) and out[a][c] (bra transform) distributed over
 //     the lanes, W passed through shared memory between the two transforms.
 // Loops run over runtime index tables, so one compiled kernel serves every
-// class pair.  Used for the FP64 path of the heavy classes and for explicit
-// quartet lists (Schwarz diagonal, debug dumps).
+// class pair.  Used for explicit quartet lists (Schwarz diagonal, debug dumps)
+// and as one of the autotuner's launch shapes for the J/K build.
 #pragma once
 #include "eri_core.cuh"
 

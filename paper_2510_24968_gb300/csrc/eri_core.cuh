@@ -8,8 +8,9 @@
 //             sum_{tuv} sum_{tau nu phi} (-1)^{tau+nu+phi} E^{ab}_{tuv} E^{cd}_{tau nu phi}
 //             R^0_{t+tau, u+nu, v+phi}(alpha = pq/(p+q), P - Q)
 // with R^0 from the recursion of Eq. R-recursion seeded by the Boys function.
-// Evaluation order (per thread = one shell quartet, ket components in chunks
-// of CS so that the per-thread arrays stay in registers):
+// Evaluation order (per thread = one shell quartet, or a share of its bra
+// primitive pairs / ket chunks; ket components in chunks of CS so that R, W and
+// the chunk's E non-zeros stay in registers; out lives in shared memory):
 //   for each bra primitive pair b:
 //     W[h][c] = sum_k sum_{h' in nz(c)} sign(h') E^{cd,k}_{h'} R^{bk}[h + h']   (ket transform)
 //     out[a][c] += sum_{h in nz(a)} E^{ab,b}_h W[h][c]                            (bra transform)
