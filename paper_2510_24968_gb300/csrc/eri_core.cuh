@@ -56,7 +56,8 @@ struct PairView {
 template <typename Real>
 struct JKMol {
   PairView<Real> bra, ket;
-  const int* __restrict__ tile_prefix;  // [nbra + 1] cumulative ket tiles per bra
+  const int* __restrict__ prefix;       // [nbra + 1] cumulative work units per bra: ket tiles
+                                        // (per-bra form) or screened quartets (flattened form)
   const int* __restrict__ ket_count;    // [nbra] screened ket prefix length per bra
   int N;
   const Real* __restrict__ D;           // density, N x N, in the working precision
@@ -248,11 +249,23 @@ __device__ __forceinline__ int find_bra(const int* __restrict__ prefix, int n, i
   return lo;
 }
 
-// Fused ERI + J/K kernel, persistent: each CTA walks work items (bra pair,
-// tile of kets) with a grid stride; threads = (ket chunk group, ket,
-// bra-primitive subset).
+// Fused ERI + J/K kernel, persistent: each CTA walks work items with a grid
+// stride; threads = (ket chunk group, quartet of the tile, bra-primitive
+// subset).  Two work decompositions (compile-time, by precision):
+//  * FP32 (kFlat false): a work item is (bra pair, tile of its screened kets).
+//    The CTA stages the bra's primitive data and D block in shared memory,
+//    where every thread reads them as broadcasts, and reduces J_bra over the
+//    CTA (one FP64 add per element and item).
+//  * FP64 (kFlat true): a work item is a tile of consecutive quartets of the
+//    class pair's flattened (bra, screened ket) list, so tiles are full however
+//    few kets a bra has, and the loop has no barriers.  Each thread reads its
+//    bra data through the L1 cache and reduces J_bra over the warp when the
+//    warp's quartets share one bra (else lane by lane).  At the FP64 rate the
+//    extra loads are free and the full tiles and missing barriers win (5-26 %
+//    per class on the 12-atom cloud); at the FP32 rate the per-bra staging is
+//    faster (up to 1.9x on the 30-atom cloud).
 // Shared memory: the Boys table columns L..L+K-1 (loaded once per CTA), the
-// bra block of D, the bra block of J_acc and the bra primitive data.
+// per-thread quartet-block and J_bra slots, and (per-bra form) the bra block.
 // Accumulates J_acc, K_acc with the 8-fold degeneracy factor; the caller
 // symmetrises J = (J_acc + J_acc^T)/4 and K = (K_acc + K_acc^T)/8.
 template <typename Real>
@@ -260,66 +273,107 @@ __host__ __device__ constexpr size_t jk_boys_smem() {
   return (size_t)Boys<Real>::NROW * Boys<Real>::K * sizeof(Real);
 }
 
+template <typename Real>
+__host__ __device__ constexpr bool jk_flat() {
+  return sizeof(Real) == 8;
+}
+
+// Dynamic shared memory of one CTA (bra_ppmax: largest bra primitive-pair count).
+template <typename Real, int LA, int LB, int CS>
+__host__ __device__ constexpr size_t jk_smem_bytes(int bra_ppmax) {
+  using BC = PairCls<LA, LB>;
+  return (jk_boys_smem<Real>() + 15) / 16 * 16 + (size_t)(CS + 1) * BC::NC * kJKThreads * sizeof(Real) +
+         (jk_flat<Real>() ? 0
+                          : ((1 + kJKThreads / 32) * BC::NC + (size_t)bra_ppmax * (4 + BC::NNZ)) * sizeof(Real));
+}
+
 template <typename Real, int LA, int LB, int LC, int LD, int CS>
 __global__ void __launch_bounds__(kJKThreads) jk_kernel(JKParams<Real> P) {
   using BC = PairCls<LA, LB>;
   using KC = PairCls<LC, LD>;
+  constexpr bool kFlat = jk_flat<Real>();
   constexpr int L = LA + LB + LC + LD;
   constexpr int NFB = 4 + BC::NNZ;
   constexpr int BK = Boys<Real>::K, BR = Boys<Real>::NROW;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int NWARP = kJKThreads / 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* sBoys = reinterpret_cast<Real*>(smem_raw);                     // [BR][BK]
-  Real* sDab = reinterpret_cast<Real*>(smem_raw + (jk_boys_smem<Real>() + 15) / 16 * 16);  // D bra block
-  Real* sJw = sDab + BC::NC;               // per-warp partials of J_acc for the bra block [warp][a]
-  Real* sOut = sJw + NWARP * BC::NC;       // per-thread quartet chunk out(a, cs) [a * CS + cs][thread]
+  Real* sOut = reinterpret_cast<Real*>(smem_raw + (jk_boys_smem<Real>() + 15) / 16 * 16);  // [a * CS + cs][thread]
   Real* sJb = sOut + BC::NC * CS * kJKThreads;  // per-thread part of J_acc for the bra block [a][thread]
-  Real* sbra = sJb + BC::NC * kJKThreads;  // bra primitive data [pp][field]
+  Real* sDab = sJb + BC::NC * kJKThreads;       // per-bra form: D bra block [a]
+  Real* sJw = sDab + BC::NC;                    // per-bra form: per-warp J_bra partials [warp][a]
+  Real* sbra = sJw + NWARP * BC::NC;            // per-bra form: bra primitive data [pp][field]
 
   for (int x = threadIdx.x; x < BR * BK; x += blockDim.x)
     sBoys[x] = P.boys[(x / BK) * kBoysCols + L + x % BK];
-  // thread = (chunk group cg, ket q of the tile, bra-primitive subset bs); the
-  // chunk group is the slowest index, so it is uniform within each warp
+  __syncthreads();
+  // thread = (chunk group cg, quartet q of the tile, bra-primitive subset bs);
+  // the chunk group is the slowest index, so it is uniform within each warp
   const int ps = P.psplit, ncg = P.csplit;
   const int gsz = blockDim.x / ncg;
   const int cg = threadIdx.x / gsz, t = threadIdx.x % gsz;
   const int tq = gsz / ps;
   const int q = t / ps, bs = t % ps;
   const int lane = threadIdx.x & 31;
+  Real* so = sOut + threadIdx.x;
+  Real* jb = sJb + threadIdx.x;  // this thread's part of J_acc for its bra block, jb[a * kJKThreads]
 
   for (int item = blockIdx.x; item < P.nitems; item += gridDim.x) {
     int litem = item;
     const JKMol<Real>* Mp = &P.one;
     if (P.nmol > 0) {
       const int m = find_bra(P.mol_prefix, P.nmol, item);
-      if (P.active && !__ldg(P.active + __ldg(P.mol_ids + m))) continue;  // uniform per CTA: skip a converged molecule
+      if (P.active && !__ldg(P.active + __ldg(P.mol_ids + m))) continue;  // uniform per CTA: a converged molecule
       Mp = P.mols + m;
       litem = item - __ldg(P.mol_prefix + m);
     }
     const JKMol<Real> M = *Mp;
     const int N = M.N;
-    const int i = find_bra(M.tile_prefix, M.bra.n, litem);
-    const int tile = litem - __ldg(M.tile_prefix + i);
-    const int4 bi = M.bra.idx[i];
-    const int nppb = M.bra.npp[i];
-    __syncthreads();  // previous item done with the bra buffers
-    for (int x = threadIdx.x; x < nppb * NFB; x += blockDim.x) {
-      const int pp = x / NFB, f = x % NFB;
-      sbra[x] = M.bra.pd[((size_t)f * M.bra.ppmax + pp) * M.bra.n + i];
+    // this thread's quartet (bra i, ket j), if any
+    int i = -1, j = 0;
+    bool valid;
+    if constexpr (kFlat) {
+      const int g = litem * tq + q;  // quartet index in the flattened list
+      valid = q < tq && g < __ldg(M.prefix + M.bra.n);
+      if (valid) {
+        i = find_bra(M.prefix, M.bra.n, g);
+        j = g - __ldg(M.prefix + i);
+      }
+    } else {
+      i = find_bra(M.prefix, M.bra.n, litem);
+      const int tile = litem - __ldg(M.prefix + i);
+      const int nppb = M.bra.npp[i];
+      const int4 bb = M.bra.idx[i];
+      __syncthreads();  // previous item done with the bra buffers
+      for (int x = threadIdx.x; x < nppb * NFB; x += blockDim.x) {
+        const int pp = x / NFB, f = x % NFB;
+        sbra[x] = M.bra.pd[((size_t)f * M.bra.ppmax + pp) * M.bra.n + i];
+      }
+      for (int x = threadIdx.x; x < BC::NC; x += blockDim.x)
+        sDab[x] = M.D[(size_t)(bb.x + x / BC::NB) * N + bb.y + x % BC::NB];
+      __syncthreads();
+      j = tile * tq + q;
+      valid = q < tq && j < __ldg(M.ket_count + i);
     }
-    for (int x = threadIdx.x; x < BC::NC; x += blockDim.x) sDab[x] = M.D[(size_t)(bi.x + x / BC::NB) * N + bi.y + x % BC::NB];
-    __syncthreads();
-
-    const int j = tile * tq + q;
-    Real* so = sOut + threadIdx.x;
-    Real* jb = sJb + threadIdx.x;  // this thread's part of J_acc for the bra block, jb[a * kJKThreads]
+    const int4 bi = i >= 0 ? M.bra.idx[i] : make_int4(0, 0, 0, 0);
 #pragma unroll
     for (int a = 0; a < BC::NC; ++a) jb[a * kJKThreads] = Real(0);
-    if (q < tq && j < __ldg(M.ket_count + i)) {
+    if (valid) {
       const int4 ki = M.ket.idx[j];
+      const int nppb = M.bra.npp[i];
       const int nppk = M.ket.npp[j];
       const Real deg = Real((bi.z == bi.w ? 1 : 2) * (ki.z == ki.w ? 1 : 2) * ((P.same && i == j) ? 1 : 2));
-      auto bra = [&](int f, int pp) -> Real { return sbra[pp * NFB + f]; };
+      const size_t bstride = (size_t)M.bra.ppmax * M.bra.n;
+      const Real* bpd = M.bra.pd + i;
+      const Real* Dbra = M.D + (size_t)bi.x * N + bi.y;
+      auto bra = [&](int f, int pp) -> Real {
+        if constexpr (kFlat) return __ldg(bpd + (size_t)f * bstride + (size_t)pp * M.bra.n);
+        else return sbra[pp * NFB + f];
+      };
+      auto Dab = [&](int a) -> Real {
+        if constexpr (kFlat) return __ldg(Dbra + (size_t)(a / BC::NB) * N + a % BC::NB);
+        else return sDab[a];
+      };
 #pragma unroll 1
       for (int ch = cg; ch < KetChunks<KC, CS>::NCH; ch += ncg) {
         quartet_chunk<Real, LA, LB, LC, LD, CS>(so, bra, nppb, bs, ps, M.ket, j, nppk, sBoys, BK, P.boys64_T, ch);
@@ -336,7 +390,7 @@ __global__ void __launch_bounds__(kJKThreads) jk_kernel(JKParams<Real> P) {
 #pragma unroll
           for (int a = 0; a < BC::NC; ++a) {
             const Real v = deg * out(a, cs);
-            jk = fma(sDab[a], v, jk);
+            jk = fma(Dab(a), v, jk);
             jb[a * kJKThreads] = fma(Dls, v, jb[a * kJKThreads]);
           }
           atomicAdd(&M.J[(size_t)lam * N + sig], (double)jk);
@@ -372,22 +426,43 @@ __global__ void __launch_bounds__(kJKThreads) jk_kernel(JKParams<Real> P) {
         }
       }
     }
-    // J_bra: warp reduction (every lane takes part, idle lanes hold zeros), one
-    // shared-memory partial per warp and element, one FP64 global add per CTA
-    // and element
-    const int warp = threadIdx.x >> 5;
+    if constexpr (kFlat) {
+      // J_bra: when every active lane of the warp holds lane 0's bra, a warp
+      // reduction and one FP64 add per element; otherwise each lane adds its own
+      const int i0 = __shfl_sync(0xffffffffu, i, 0);
+      if (__all_sync(0xffffffffu, i == i0 || i < 0)) {
+        if (i0 >= 0) {
 #pragma unroll
-    for (int a = 0; a < BC::NC; ++a) {
-      Real v = jb[a * kJKThreads];
+          for (int a = 0; a < BC::NC; ++a) {
+            Real v = jb[a * kJKThreads];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) sJw[warp * BC::NC + a] = v;
-    }
-    __syncthreads();
-    for (int x = threadIdx.x; x < BC::NC; x += blockDim.x) {
-      double v = 0.0;
-      for (int w = 0; w < NWARP; ++w) v += (double)sJw[w * BC::NC + x];
-      atomicAdd(&M.J[(size_t)(bi.x + x / BC::NB) * N + bi.y + x % BC::NB], v);
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) atomicAdd(&M.J[(size_t)(bi.x + a / BC::NB) * N + bi.y + a % BC::NB], (double)v);
+          }
+        }
+      } else if (i >= 0) {
+#pragma unroll
+        for (int a = 0; a < BC::NC; ++a)
+          atomicAdd(&M.J[(size_t)(bi.x + a / BC::NB) * N + bi.y + a % BC::NB], (double)jb[a * kJKThreads]);
+      }
+    } else {
+      // J_bra: warp reduction (every lane takes part, idle lanes hold zeros), one
+      // shared-memory partial per warp and element, one FP64 global add per CTA
+      // and element
+      const int warp = threadIdx.x >> 5;
+#pragma unroll
+      for (int a = 0; a < BC::NC; ++a) {
+        Real v = jb[a * kJKThreads];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sJw[warp * BC::NC + a] = v;
+      }
+      __syncthreads();
+      for (int x = threadIdx.x; x < BC::NC; x += blockDim.x) {
+        double v = 0.0;
+        for (int w = 0; w < NWARP; ++w) v += (double)sJw[w * BC::NC + x];
+        atomicAdd(&M.J[(size_t)(bi.x + x / BC::NB) * N + bi.y + x % BC::NB], v);
+      }
     }
   }
 }

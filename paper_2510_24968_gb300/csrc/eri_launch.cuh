@@ -19,9 +19,7 @@ cudaError_t launch_jk(const JKParams<Real>& p, cudaStream_t s) {
   static_assert((size_t)(CS + 1) * BC::NC * kJKThreads * sizeof(Real) <= kJKBlockSmemMax,
                 "per-thread quartet blocks exceed the shared-memory budget");
   auto k = jk_kernel<Real, LA, LB, LC, LD, CS>;
-  const size_t smem = (jk_boys_smem<Real>() + 15) / 16 * 16 + (1 + kJKThreads / 32) * BC::NC * sizeof(Real) +
-                      (size_t)(CS + 1) * BC::NC * kJKThreads * sizeof(Real) +
-                      (size_t)p.bra_ppmax * (4 + BC::NNZ) * sizeof(Real);
+  const size_t smem = jk_smem_bytes<Real, LA, LB, CS>(p.bra_ppmax);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (p.nitems == 0) return cudaSuccess;

@@ -5,7 +5,8 @@
 // each bra pair i (pairs of a class sorted by Schwarz bound Q, descending),
 // the kets that survive Q_i Q_j >= tau form a prefix of class Y; with X == Y
 // the prefix is cut at j <= i so each unique quartet appears once.  A work
-// item is (bra, tile of consecutive kets); one CTA per item.
+// item is (bra, tile of consecutive kets), or for the FP64 kernels a tile of
+// consecutive quartets of the flattened (bra, ket) list.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -125,7 +126,7 @@ static long long screened_counts(const fsim_basis* b, int X, int Y, double tau, 
 // unrolled kernel psplit threads per quartet share the bra primitive pairs and
 // csplit thread groups share the ket chunks; or the cooperative kernel.
 int set_class_plan(fsim_basis* b, int X, int Y, const std::vector<int>& count, int psplit, int coop,
-                   ClassPairPlan& cp, int csplit) {
+                   ClassPairPlan& cp, int csplit, int flat) {
   const DevClass& CX = b->cls[X];
   if (!coop && !(psplit >= 1 && psplit <= kJKThreads / 4 && (csplit == 1 || csplit == 2 || csplit == 4))) {
     set_error("bad launch shape (%d|%d): psplit %d, csplit %d", X, Y, psplit, csplit);
@@ -135,9 +136,21 @@ int set_class_plan(fsim_basis* b, int X, int Y, const std::vector<int>& count, i
   cp.psplit = coop ? 1 : psplit;
   cp.csplit = coop ? 1 : csplit;
   cp.tq = coop ? kCoopWarps : (kJKThreads / cp.csplit) / cp.psplit;
+  // tiles per bra (prefix of tile counts: cooperative kernel, per-bra form of
+  // the unrolled kernel) or tiles of the flattened (bra, ket) list (prefix of
+  // quartet counts: flattened form)
+  const bool fl = flat && !coop;
   std::vector<int> prefix(CX.n + 1, 0);
-  for (int i = 0; i < CX.n; ++i) prefix[i + 1] = prefix[i] + (count[i] + cp.tq - 1) / cp.tq;
-  cp.nitems = prefix[CX.n];
+  long long acc = 0;
+  for (int i = 0; i < CX.n; ++i) {
+    acc += fl ? count[i] : (count[i] + cp.tq - 1) / cp.tq;
+    if (acc > 2147483647LL - kJKThreads) {
+      set_error("class pair (%d|%d): more than 2^31 screened quartets; shard the build", X, Y);
+      return FSIM_EINVAL;
+    }
+    prefix[i + 1] = (int)acc;
+  }
+  cp.nitems = fl ? (prefix[CX.n] + cp.tq - 1) / cp.tq : prefix[CX.n];
   if (!cp.d_prefix) FSIM_TRY(dev_alloc(&cp.d_prefix, CX.n + 1));
   if (!cp.d_count) FSIM_TRY(dev_alloc(&cp.d_count, CX.n));
   FSIM_CK(cudaMemcpy(cp.d_prefix, prefix.data(), sizeof(int) * (CX.n + 1), cudaMemcpyHostToDevice));
@@ -186,7 +199,7 @@ int get_plan(fsim_basis* b, double tau, int shard, int nshards, int precision, F
             if (cp.nquartets * ps * cs < target && c <= nch) cs = c;
         }
       }
-      FSIM_TRY(set_class_plan(b, X, Y, count, ps, coop, cp, cs));
+      FSIM_TRY(set_class_plan(b, X, Y, count, ps, coop, cp, cs, jk_flat_precision(precision)));
       P->nquartets += cp.nquartets;
     }
   *out = P;
@@ -705,7 +718,8 @@ static int autotune_impl(fsim_basis* b, FockPlan* plan, const Real* Dr, float b6
       Cand win = cands[0];
       ClassPairPlan tmp;
       for (const Cand& c : cands) {
-        if ((rc = set_class_plan(b, X, Y, count, c.psplit, c.coop, tmp, c.csplit)) != FSIM_OK) break;
+        if ((rc = set_class_plan(b, X, Y, count, c.psplit, c.coop, tmp, c.csplit, jk_flat<Real>())) != FSIM_OK)
+          break;
         float t[3];
         cudaError_t e = launch_cp<Real>(b, X, Y, tmp, Dr, b->d_Jacc, b->d_Kacc, b64, s);  // warm-up
         for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
@@ -729,7 +743,7 @@ static int autotune_impl(fsim_basis* b, FockPlan* plan, const Real* Dr, float b6
       dev_free(tmp.d_prefix);
       dev_free(tmp.d_count);
       if (rc != FSIM_OK) break;
-      rc = set_class_plan(b, X, Y, count, win.psplit, win.coop, cp, win.csplit);
+      rc = set_class_plan(b, X, Y, count, win.psplit, win.coop, cp, win.csplit, jk_flat<Real>());
       if (choice) choice[ci] = win.coop ? -1 : 10 * win.psplit + win.csplit;
       if (best_ms) best_ms[ci] = best;
     }

@@ -239,7 +239,9 @@ struct fsim_basis {
 namespace fsim {
 int get_plan(fsim_basis* b, double tau, int shard, int nshards, int precision, FockPlan** out, int psplit_force);
 int set_class_plan(fsim_basis* b, int X, int Y, const std::vector<int>& count, int psplit, int coop,
-                   ClassPairPlan& cp, int csplit = 1);
+                   ClassPairPlan& cp, int csplit, int flat);
+// the unrolled kernel's work decomposition of a precision (see jk_kernel)
+inline int jk_flat_precision(int precision) { return precision == FSIM_FP64 ? (int)jk_flat<double>() : (int)jk_flat<float>(); }
 int ensure_scratch(fsim_basis* b);
 int ensure_schwarz(fsim_basis* b);
 int device_sm_count();
