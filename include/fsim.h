@@ -275,7 +275,9 @@ void fsim_batch_destroy(fsim_batch* batch);
  * algebra spread over several streams; converged molecules drop out.  Same
  * options and per-molecule semantics as fsim_scf (core-H guess only; each
  * molecule's electron count is its nuclear charge).  results: nmol entries;
- * time_s is the time at which that molecule converged.
+ * time_s is the time from the start of the iteration loop (after the set-up:
+ * one-electron matrices, orthogonaliser, guess, batch plans) at which that
+ * molecule converged; t_hist counts from the start of the call.
  */
 int fsim_scf_batched(fsim_basis* const* bases, int nmol, const fsim_scf_opts* opts, fsim_scf_result* results);
 

@@ -5,7 +5,9 @@
 Draws `nmol` molecules with U{nmin..nmax} heavy atoms (fsim_synth.batched_set),
 runs fsim_scf_batched on them (mixed precision by default) and prints one JSON
 object: wall time, molecules/s, converged count, p50/p99 of the per-molecule
-times and the mean iteration count.  Every step runs in libfsim.
+times, the mean iteration count, and the end time of the first iteration (set-up
+included) and the length of each later lockstep iteration.  Every step runs in
+libfsim.
 """
 from __future__ import annotations
 
@@ -47,6 +49,8 @@ def main(argv=None):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     ts = sorted(r["time_s"] for r in res)
+    # lockstep: every molecule still iterating shares the iteration end times
+    th = max((r["times"] for r in res), key=len)
     print(json.dumps({
         "nmol": a.nmol, "heavy_atoms": [a.nmin, a.nmax], "nbf_range": [min(b.nbf for b in bases),
                                                                      max(b.nbf for b in bases)],
@@ -55,6 +59,8 @@ def main(argv=None):
         "p50_s": ts[len(ts) // 2], "p99_s": ts[min(len(ts) - 1, int(0.99 * len(ts)))],
         "mean_iters": float(np.mean([r["iters"] for r in res])),
         "fp64_builds": int(sum(r["fp64_builds"] for r in res)),
+        "first_iteration_end_s": float(th[0]) if len(th) else None,
+        "iteration_s": [float(x) for x in np.diff(th)],
     }))
 
 

@@ -156,12 +156,20 @@ int build_tables(fsim_batch* bt, int prec) {
   return FSIM_OK;
 }
 
+// dry = true: no launch; every kernel of the sequence has its attributes set
+// and its module loaded, so that the sequence can then be captured directly.
 template <typename Real>
-int launch_batch(fsim_batch* bt, int prec, cudaStream_t s) {
+int launch_batch(fsim_batch* bt, int prec, cudaStream_t s, bool dry) {
   const int mixed = prec == 1;
   dim3 g(std::max(1, std::min(64, (bt->maxN * bt->maxN + 255) / 256)), bt->nmol);
-  batch_prepare_kernel<<<g, 256, 0, s>>>(bt->d_ptrs, bt->d_active, mixed);
-  FSIM_CK(cudaGetLastError());
+  if (dry) {
+    cudaFuncAttributes fa;
+    FSIM_CK(cudaFuncGetAttributes(&fa, batch_prepare_kernel));
+    FSIM_CK(cudaFuncGetAttributes(&fa, batch_symmetrize_kernel));
+  } else {
+    batch_prepare_kernel<<<g, 256, 0, s>>>(bt->d_ptrs, bt->d_active, mixed);
+    FSIM_CK(cudaGetLastError());
+  }
   for (int X = kNumPairCls - 1; X >= 0; --X)
     for (int Y = X; Y >= 0; --Y) {
       const fsim_batch::CPB& C = bt->cp[prec][X][Y];
@@ -174,7 +182,7 @@ int launch_batch(fsim_batch* bt, int prec, cudaStream_t s) {
         p.active = bt->d_active;
         p.mol_ids = C.d_ids;
         p.nmol = C.nin;
-        p.nitems = C.nitems;
+        p.nitems = dry ? 0 : C.nitems;
         p.same = X == Y ? 1 : 0;
         p.psplit = 1;
         p.csplit = 1;
@@ -188,14 +196,15 @@ int launch_batch(fsim_batch* bt, int prec, cudaStream_t s) {
         return FSIM_ECUDA;
       }
     }
+  if (dry) return FSIM_OK;
   dim3 g2(std::max(1, std::min(64, (bt->maxN * bt->maxN + 255) / 256)), bt->nmol);
   batch_symmetrize_kernel<<<g2, 256, 0, s>>>(bt->d_ptrs, bt->d_active);
   FSIM_CK(cudaGetLastError());
   return FSIM_OK;
 }
 
-int launch_prec(fsim_batch* bt, int prec, cudaStream_t s) {
-  return prec == 0 ? launch_batch<double>(bt, 0, s) : launch_batch<float>(bt, 1, s);
+int launch_prec(fsim_batch* bt, int prec, cudaStream_t s, bool dry = false) {
+  return prec == 0 ? launch_batch<double>(bt, 0, s, dry) : launch_batch<float>(bt, 1, s, dry);
 }
 
 }  // namespace
@@ -277,8 +286,9 @@ int fsim_batch_fock(fsim_batch* bt, int precision, const int* active, int use_gr
   if (active) FSIM_CK(cudaMemcpyAsync(bt->d_active, active, sizeof(int) * bt->nmol, cudaMemcpyHostToDevice, s));
   if (!use_graph) return launch_prec(bt, prec, s);
   if (!bt->exec[prec]) {
-    // one eager build settles attributes and caches, then capture the same sequence
-    FSIM_TRY(launch_prec(bt, prec, s));
+    // a dry pass sets the kernels' attributes (outside the capture), then the
+    // sequence is captured once and replayed
+    FSIM_TRY(launch_prec(bt, prec, s, true));
     cudaStream_t cs;
     FSIM_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     FSIM_CK(cudaStreamSynchronize(s));
@@ -664,7 +674,7 @@ extern "C" int fsim_scf_batched(fsim_basis* const* bases, int nmol, const fsim_s
       Mol& m = mols[i];
       if (m.conv) continue;
       if (results[i].e_hist && m.iters < o.max_iter) results[i].e_hist[m.iters] = m.E + m.e_nuc;
-      if (results[i].t_hist && m.iters < o.max_iter) results[i].t_hist[m.iters] = now;
+      if (results[i].t_hist && m.iters < o.max_iter) results[i].t_hist[m.iters] = now + t_loop0;
       ++m.iters;
       const double rmsD = std::sqrt(hs[(size_t)i * kSlots + 1] / (double)m.n2);
       const double dE = m.have_old ? std::fabs(m.E - m.E_old) : 1e300;

@@ -371,10 +371,11 @@ def scf_batched(bases, precision=FSIM_MIXED, tau=1e-10, max_iter=100, conv_dE=1e
     o.final_fp64, o.incremental = int(final_fp64), int(incremental)
     res = (fsim_scf_result * n)()
     hist = [np.full(max_iter, np.nan) for _ in range(n)]
-    for r, h in zip(res, hist):
-        r.e_hist = _dptr(h)
+    thist = [np.full(max_iter, np.nan) for _ in range(n)]
+    for r, h, t in zip(res, hist, thist):
+        r.e_hist, r.t_hist = _dptr(h), _dptr(t)
     hb = (C.c_void_p * n)(*[b.h.value for b in bases])
     rc = _check(load().fsim_scf_batched(hb, n, C.byref(o), res), allow=(FSIM_ENOCONV,))
     return [{"e_total": r.e_total, "iters": r.iters, "converged": bool(r.converged), "time_s": r.time_s,
              "fp64_builds": r.fp64_builds, "mixed_builds": r.mixed_builds, "rc": rc,
-             "energies": h[:r.iters].copy()} for r, h in zip(res, hist)]
+             "energies": h[:r.iters].copy(), "times": t[:r.iters].copy()} for r, h, t in zip(res, hist, thist)]
