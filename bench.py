@@ -241,7 +241,7 @@ def run_ours(args):
     import torch
 
     from fsim_synth import workload
-    from paper_2510_24968_gb300 import FSIM_FP64, FSIM_MIXED, Basis
+    from paper_2510_24968_gb300 import FSIM_DFLOAT, FSIM_FP64, FSIM_MIXED, Basis
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -261,6 +261,9 @@ def run_ours(args):
     gb = Basis(mol)
     gb.schwarz()
     tuned = gb.autotune(tau=args.tau, precision=FSIM_MIXED, shard=rank, nshards=world) if not args.no_tune else {}
+    # the FP64-accurate builds get the same treatment (their plans also serve the SCF runs)
+    tuned_64 = {p: gb.autotune(tau=args.tau, precision=p, shard=rank, nshards=world)
+                for p in (FSIM_FP64, FSIM_DFLOAT)} if not args.no_tune else {}
     N = gb.nbf
     Dn = np.random.default_rng(0).standard_normal((N, N)) * 0.05
     Dn = Dn + Dn.T
@@ -317,6 +320,7 @@ def run_ours(args):
     ms_mixed, q_mixed, cls_mixed, launches, qcls = timed(FSIM_MIXED, args.steps, args.warmup)
     clk = clocks.stop()
     ms_fp64, q_fp64, cls_fp64, _, _ = timed(FSIM_FP64, max(2, min(args.steps, 3)), 1)
+    ms_df, q_df, cls_df, _, _ = timed(FSIM_DFLOAT, max(2, min(args.steps, 3)), 1)
 
     # roofline of the dominant kernel (largest time share of the mixed build)
     tot = {k: sum(v) for k, v in cls_mixed.items()}
@@ -346,17 +350,25 @@ def run_ours(args):
     if rank == 0 and not args.no_scf:
         r64 = gb.scf(precision=FSIM_FP64, tau=args.tau, stream=sptr)
         rmx = gb.scf(precision=FSIM_MIXED, tau=args.tau, stream=sptr)
+        # mixed with double-float resets (FP64-accurate builds on the FP32 pipe)
+        rdf = gb.scf(precision=FSIM_MIXED, tau=args.tau, stream=sptr, final_fp64=2)
         tte = {"fp64_s": time_to_energy(r64, r64["e_total"]), "mixed_s": time_to_energy(rmx, r64["e_total"]),
+               "mixed_dfloat_resets_s": time_to_energy(rdf, r64["e_total"]),
                "fp64_iters": r64["iters"], "mixed_iters": rmx["iters"], "mixed_fp64_builds": rmx["fp64_builds"],
-               "mixed_vs_fp64_eh": rmx["e_total"] - r64["e_total"], "e_total_fp64": r64["e_total"]}
+               "mixed_dfloat_resets_iters": rdf["iters"], "mixed_dfloat_resets_builds": rdf["fp64_builds"],
+               "mixed_vs_fp64_eh": rmx["e_total"] - r64["e_total"],
+               "mixed_dfloat_resets_vs_fp64_eh": rdf["e_total"] - r64["e_total"], "e_total_fp64": r64["e_total"]}
         gold = os.path.join(ROOT, "tests", "golden", "water8_scf_oracle.json")
         if os.path.exists(gold):
             with open(gold) as f:
                 g = json.load(f)
             tte["fp64_vs_oracle_eh"] = r64["e_total"] - g["e_total"]
             tte["mixed_vs_oracle_eh"] = rmx["e_total"] - g["e_total"]
+            tte["mixed_dfloat_resets_vs_oracle_eh"] = rdf["e_total"] - g["e_total"]
         if tte["fp64_s"] and tte["mixed_s"]:
             tte["speedup"] = tte["fp64_s"] / tte["mixed_s"]
+        if tte["fp64_s"] and tte["mixed_dfloat_resets_s"]:
+            tte["speedup_dfloat_resets"] = tte["fp64_s"] / tte["mixed_dfloat_resets_s"]
 
     if rank != 0:
         if world > 1:
@@ -371,8 +383,11 @@ def run_ours(args):
                    "precision": "mixed: FP32 Boys/R/contraction, FP64 J/K accumulation",
                    "step": "one Fock build J,K <- D", "l2": "256 MiB write before every timed step",
                    "parallelism": f"bra-pair shards x{world}" if world > 1 else "1 GPU"},
-        "fock_builds_per_s": {"mixed": 1e3 / ms_mixed, "fp64": 1e3 / ms_fp64},
-        "eri_quartets_per_s": {"mixed": value, "fp64": q_fp64 / (ms_fp64 * 1e-3)},
+        "fock_builds_per_s": {"mixed": 1e3 / ms_mixed, "fp64": 1e3 / ms_fp64, "dfloat": 1e3 / ms_df},
+        "eri_quartets_per_s": {"mixed": value, "fp64": q_fp64 / (ms_fp64 * 1e-3), "dfloat": q_df / (ms_df * 1e-3)},
+        "class_ms_fp64_dfloat": {f"{names[k[0]]}|{names[k[1]]}": [round(sum(cls_fp64[k]) / len(cls_fp64[k]), 3),
+                                                                  round(sum(cls_df[k]) / len(cls_df[k]), 3)]
+                                 for k in cls_fp64 if k in cls_df},
         "time_to_energy_1e-8": tte,
         "roofline": {"kernel": f"jk_kernel<float> ({names[dom[0]]}|{names[dom[1]]})", "bound": "alu",
                      "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -387,6 +402,9 @@ def run_ours(args):
                            "frac_fp64": all_fl / (ms_fp64 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS},
         "class_ms": {f"{names[k[0]]}|{names[k[1]]}": round(tot[k] / len(cls_mixed[k]), 4) for k in tot},
         "autotune": {f"{names[k[0]]}|{names[k[1]]}": v[0] for k, v in tuned.items()},
+        "autotune_fp64_dfloat": {f"{names[k[0]]}|{names[k[1]]}": [tuned_64[FSIM_FP64].get(k, (0,))[0],
+                                                                  tuned_64[FSIM_DFLOAT].get(k, (0,))[0]]
+                                 for k in tuned} if tuned_64 else {},
         "cpu_baseline": cpu,
         "e2e": {"value": q_mixed / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * N * 8,
                 "d2h_bytes_per_step": 2 * N * N * 8},

@@ -39,6 +39,14 @@ extern "C" {
 
 #define FSIM_FP64 0   /* every step in FP64 */
 #define FSIM_MIXED 1  /* FP32 Boys, Hermite integrals and contraction; FP64 J/K accumulation */
+/* FP64-accurate integrals with the light class pairs in double-float
+ * arithmetic: each value an unevaluated sum of two FP32 numbers (~2^-47
+ * relative rounding, FP32 exponent range) on the FP32 pipe, FP64 J/K
+ * accumulation.  By default class pairs of total angular momentum <= 4 run the
+ * double-float kernel and the others the FP64 kernel (fsim_autotune times
+ * both).  Exponent range: products (2 p q / (p + q))^n up to n = 8 must stay
+ * below FP32's 3.4e38, as on the FSIM_MIXED path. */
+#define FSIM_DFLOAT 2
 
 #define FSIM_PTR_HOST 0
 #define FSIM_PTR_DEVICE 1
@@ -121,7 +129,7 @@ int fsim_schwarz(fsim_basis* b, double* Q);
 
 typedef struct {
   double schwarz_tau;  /* skip unique quartets with Q_ab Q_cd < tau; 0 = no screening */
-  int precision;       /* FSIM_FP64 or FSIM_MIXED */
+  int precision;       /* FSIM_FP64, FSIM_MIXED or FSIM_DFLOAT */
   double boys_fp64_T;  /* mixed path: Boys in FP64 for T >= this; 0 = never; values in (0, 30) are rejected */
   int ptr_mode;        /* FSIM_PTR_HOST or FSIM_PTR_DEVICE for D, J, K */
   void* stream;        /* cudaStream_t; NULL = legacy default stream */
@@ -174,12 +182,26 @@ int fsim_fock_build_noalloc(fsim_basis* b, const double* D, double* J, double* K
  * shared out over csplit = 1, 2 or 4 warp groups (a CTA of 128 threads takes
  * 128 / csplit / psplit kets), and the warp-cooperative kernel (4 kets per
  * CTA) -- and keeps the fastest in the basis' cached plan, which later
- * fsim_fock_build calls with the same options use.  choice (36 entries,
- * optional): 10 * psplit + csplit for the unrolled kernel, -1 for the
- * cooperative kernel, 0 for class pairs without work; best_ms (36,
- * optional): its median time.  Index X*6+Y as in fsim_last_class_times.
+ * fsim_fock_build calls with the same options use.  FSIM_DFLOAT: every shape
+ * with the double-float kernel and with the FP64 kernel (both FP64-accurate),
+ * no cooperative kernel.  choice (36 entries, optional): 10 * psplit + csplit
+ * for the unrolled kernel (+ 100 when a double-float build runs the class pair
+ * with the FP64 kernel), -1 for the cooperative kernel, 0 for class pairs
+ * without work; best_ms (36, optional): its median time.  Index X*6+Y as in
+ * fsim_last_class_times.
  */
 int fsim_autotune(fsim_basis* b, const fsim_fock_opts* opts, int* choice, float* best_ms);
+
+/*
+ * Sets launch shapes in the basis' cached plan for these options (screening,
+ * precision, shard), e.g. choices saved from an earlier fsim_autotune.
+ * choice: 36 host ints in fsim_autotune's encoding; 0 leaves a class pair as
+ * it is.  Errors (FSIM_EINVAL, plan unchanged for that and later class pairs):
+ * psplit not 1/3/9 or above the class's primitive pairs, csplit not 1/2/4 or
+ * above its ket chunks, the cooperative kernel with FSIM_DFLOAT, +100 outside
+ * FSIM_DFLOAT, or the double-float kernel for (dd|dp) and (dd|dd).
+ */
+int fsim_set_launch(fsim_basis* b, const fsim_fock_opts* opts, const int* choice);
 
 /* Unique shell quartets the last fsim_fock_build evaluated (after screening). */
 long long fsim_last_quartet_count(const fsim_basis* b);
@@ -217,7 +239,9 @@ typedef struct {
   int guess;            /* FSIM_GUESS_CORE or FSIM_GUESS_DENSITY */
   const double* D0;     /* host nbf*nbf initial density for FSIM_GUESS_DENSITY */
   fsim_fock_opts fock;  /* screening, precision and stream of the Fock builds */
-  int final_fp64;       /* FSIM_MIXED: after mixed convergence, finish with FP64 Fock builds */
+  int final_fp64;       /* FSIM_MIXED: after mixed convergence, finish with FP64-accurate Fock builds:
+                           0 never, 1 FSIM_FP64 builds, 2 FSIM_DFLOAT builds (fsim_scf_batched:
+                           any non-zero value means FSIM_FP64 builds) */
   int incremental;      /* build G(D_n) as G(D_{n-1}) + G(D_n - D_{n-1}) */
 } fsim_scf_opts;
 
@@ -230,11 +254,12 @@ typedef struct {
   int guess_fallback;   /* 1 when a supplied guess failed its trace/idempotency check and core-H was used */
   double* D_out;        /* optional caller-owned nbf*nbf host array: final density */
   double* e_hist;       /* optional caller-owned max_iter array: total energy after each Fock build */
-  double* t_hist;       /* optional caller-owned max_iter array: seconds since the call started */
+  double* t_hist;       /* optional caller-owned max_iter array: seconds from the start of the iteration
+                           loop (after the set-up) to the end of each iteration */
   double time_s;        /* wall time of the SCF loop */
   double min_s_eig;     /* smallest eigenvalue of S */
   long long quartets;   /* unique quartets evaluated over all Fock builds */
-  int fp64_builds;      /* Fock builds done in FP64 */
+  int fp64_builds;      /* FP64-accurate Fock builds (FSIM_FP64 or FSIM_DFLOAT) */
   int mixed_builds;     /* Fock builds done in mixed precision */
 } fsim_scf_result;
 
@@ -277,7 +302,7 @@ void fsim_batch_destroy(fsim_batch* batch);
  * molecule's electron count is its nuclear charge).  results: nmol entries;
  * time_s is the time from the start of the iteration loop (after the set-up:
  * one-electron matrices, orthogonaliser, guess, batch plans) at which that
- * molecule converged; t_hist counts from the start of the call.
+ * molecule converged; t_hist counts from the same point.
  */
 int fsim_scf_batched(fsim_basis* const* bases, int nmol, const fsim_scf_opts* opts, fsim_scf_result* results);
 

@@ -53,7 +53,7 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
     os.makedirs(OBJ, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     # longest first: the heaviest class pairs dominate the wall time
-    weight = lambda s: (("_dd" in s) * 4 + ("_dp" in s) * 2 + ("jk32" in s)) * -1
+    weight = lambda s: (("_dd" in s) * 4 + ("_dp" in s) * 2 + ("jk32" in s) + ("jkdf" in s) * 3) * -1
     srcs.sort(key=weight)
     jobs = jobs or max(1, os.cpu_count() or 1)
     t0 = time.time()

@@ -162,6 +162,8 @@ static cudaError_t launch_pair_data(int cls, int n, int ppmax, const int4* idx, 
 int build_pair_data(fsim_basis* b, int cls, const std::vector<int4>& order) {
   DevClass& C = b->cls[cls];
   dev_free(C.idx); dev_free(C.npp); dev_free(C.pd64); dev_free(C.pd32); dev_free(C.pq64); dev_free(C.pq32);
+  dev_free(C.pdx); dev_free(C.pqx);
+  b->dfloat_ready = false;  // the double-float copies follow the pair order; remade on next use
   C.n = (int)order.size();
   C.nnz = pair_cls_nnz(cls);
   C.h_idx = order;
@@ -181,6 +183,55 @@ int build_pair_data(fsim_basis* b, int cls, const std::vector<int4>& order) {
   FSIM_CK(cudaMemcpy(C.idx, order.data(), sizeof(int4) * C.n, cudaMemcpyHostToDevice));
   FSIM_CK(cudaMemcpy(C.npp, C.h_npp.data(), sizeof(int) * C.n, cudaMemcpyHostToDevice));
   FSIM_CK(launch_pair_data(cls, C.n, C.ppmax, C.idx, b, C.pd64, C.pd32, C.pq64, C.pq32));
+  return FSIM_OK;
+}
+
+// Double-float copies (nearest dfloat of each FP64 value) of the pair data, the
+// Boys table and a density buffer, made once on the first FSIM_DFLOAT build.
+__global__ void split_kernel(const double* __restrict__ in, dfloat* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = dsplit_rn(in[i]);
+}
+
+__global__ void split4_kernel(const double4_32a* __restrict__ in, dfloat4* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double4_32a v = in[i];
+    out[i] = dfloat4{dsplit_rn(v.x), dsplit_rn(v.y), dsplit_rn(v.z), dsplit_rn(v.w)};
+  }
+}
+
+// The double-float table keeps e^{-T_i} in its last column (an order no class
+// reaches), read by the double-float Boys function.
+__global__ void boys_exp_column_kernel(dfloat* __restrict__ tab) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kBoysN64; i += gridDim.x * blockDim.x)
+    tab[(size_t)i * kBoysCols + kBoysCols - 1] = dsplit_rn(exp(-i * kBoysH64));
+}
+
+void launch_split(const double* in, dfloat* out, size_t n, cudaStream_t s) {
+  if (n) split_kernel<<<(unsigned)std::min<size_t>((n + 255) / 256, 1024), 256, 0, s>>>(in, out, n);
+}
+
+int ensure_dfloat(fsim_basis* b) {
+  if (b->dfloat_ready) return FSIM_OK;
+  for (int X = 0; X < kNumPairCls; ++X) {
+    DevClass& C = b->cls[X];
+    if (C.n == 0) continue;
+    const size_t nf = (size_t)C.nfield() * C.ppmax * C.n, nq = (size_t)C.ppmax * C.n;
+    if (!C.pdx) FSIM_TRY(dev_alloc(&C.pdx, nf));
+    if (!C.pqx) FSIM_TRY(dev_alloc(&C.pqx, nq));
+    launch_split(C.pd64, C.pdx, nf, 0);
+    split4_kernel<<<(unsigned)std::min<size_t>((nq + 255) / 256, 1024), 256>>>(C.pq64, C.pqx, nq);
+  }
+  const size_t nb = (size_t)kBoysN64 * kBoysCols;
+  if (!b->d_boysx) {
+    FSIM_TRY(dev_alloc(&b->d_boysx, nb));
+    launch_split(b->d_boys64, b->d_boysx, nb, 0);
+    boys_exp_column_kernel<<<(kBoysN64 + 127) / 128, 128>>>(b->d_boysx);
+  }
+  if (!b->d_Dx) FSIM_TRY(dev_alloc(&b->d_Dx, (size_t)b->nbf * b->nbf));
+  FSIM_CK(cudaGetLastError());
+  FSIM_CK(cudaDeviceSynchronize());
+  b->dfloat_ready = true;
   return FSIM_OK;
 }
 
@@ -471,6 +522,7 @@ void fsim_basis_destroy(fsim_basis* b) {
   if (!b) return;
   for (auto& C : b->cls) {
     dev_free(C.idx); dev_free(C.npp); dev_free(C.pd64); dev_free(C.pd32); dev_free(C.pq64); dev_free(C.pq32);
+    dev_free(C.pdx); dev_free(C.pqx);
   }
   for (auto* p : b->plans) {
     for (auto& row : p->cp)
@@ -482,7 +534,7 @@ void fsim_basis_destroy(fsim_basis* b) {
   }
   dev_free(b->d_cen); dev_free(b->d_alpha); dev_free(b->d_coef); dev_free(b->d_nprim);
   dev_free(b->d_l); dev_free(b->d_ao); dev_free(b->d_axyz); dev_free(b->d_Z);
-  dev_free(b->d_boys64); dev_free(b->d_boys32);
+  dev_free(b->d_boys64); dev_free(b->d_boys32); dev_free(b->d_boysx); dev_free(b->d_Dx);
   dev_free(b->d_Jacc); dev_free(b->d_Kacc); dev_free(b->d_D); dev_free(b->d_J); dev_free(b->d_K);
   dev_free(b->d_D32);
   dev_free(b->d_sti); dev_free(b->d_stc); dev_free(b->d_sci); dev_free(b->d_scc);

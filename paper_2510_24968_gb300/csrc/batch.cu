@@ -674,7 +674,7 @@ extern "C" int fsim_scf_batched(fsim_basis* const* bases, int nmol, const fsim_s
       Mol& m = mols[i];
       if (m.conv) continue;
       if (results[i].e_hist && m.iters < o.max_iter) results[i].e_hist[m.iters] = m.E + m.e_nuc;
-      if (results[i].t_hist && m.iters < o.max_iter) results[i].t_hist[m.iters] = now + t_loop0;
+      if (results[i].t_hist && m.iters < o.max_iter) results[i].t_hist[m.iters] = now;
       ++m.iters;
       const double rmsD = std::sqrt(hs[(size_t)i * kSlots + 1] / (double)m.n2);
       const double dE = m.have_old ? std::fabs(m.E - m.E_old) : 1e300;

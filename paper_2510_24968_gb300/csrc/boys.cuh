@@ -15,8 +15,13 @@
 // in FP64 above a caller-chosen threshold `t64` (the policy of keeping Boys in
 // FP64 at large T; on GB300 FP64 issues at a small fraction of the FP32 rate,
 // so that policy is an option, not the default).
+// Double-float (dfloat): the FP64 grid and K, everything in dfloat arithmetic
+// (see boys_dfloat); no FP64 operation.
 #pragma once
 #include <cuda_runtime.h>
+
+#include "dfloat.cuh"
+#include "md_tables.cuh"
 
 namespace fsim {
 
@@ -107,11 +112,67 @@ __device__ __forceinline__ void boys_fp32(float T, float (&F)[L + 1], const floa
   }
 }
 
+// 1/k! as a double-float constant
+__host__ __device__ constexpr double inv_fact(int k) { return k <= 1 ? 1.0 : inv_fact(k - 1) / k; }
+
+// Double-float Boys function without FP64 operations.  `row` holds, for the
+// nearest grid point T_i, F_{L..L+K-1}(T_i) and in slot K the value e^{-T_i}.
+//  * T < 36: Taylor sum for F_L as in FP64; e^{-T} = e^{-T_i} e^{x},
+//    x = T_i - T in [-1/32, 1/32], e^{x} by its Taylor series to x^7 (the
+//    next term is below 2^-55); downward recursion.
+//  * T >= 36: F_0 = (1/2) sqrt(pi) T^{-1/2} (erfc(6) < 3e-17 of it), upward
+//    recursion with e^{-T} from the FP32 exponential: e^{-T} <= 2.4e-16 enters
+//    F_n at most at ~1e-8 of its size (n <= 8, T >= 36), so FP32's relative
+//    error leaves ~1e-15.
+template <int L>
+__device__ __forceinline__ void boys_dfloat(dfloat T, dfloat (&F)[L + 1], const dfloat* __restrict__ tabL,
+                                            int stride) {
+  if (T.hi < (float)kBoysTmax64) {
+    const int i = __float2int_rn(T.hi * (float)(1.0 / kBoysH64));
+    const dfloat x = dfloat((float)i * (float)kBoysH64, 0.0f) - T;  // -(T - T_i); i h is exact in FP32
+    const dfloat* row = tabL + i * stride;
+    dfloat acc = row[kBoysK64 - 1];
+    static_for<kBoysK64 - 1>([&](auto I) {
+      constexpr int k = kBoysK64 - 1 - decltype(I)::value;
+      acc = fma(acc, x * dsplit(inv_int(k)), row[k - 1]);
+    });
+    F[L] = acc;
+    if constexpr (L > 0) {
+      constexpr int kExpTerms = 7;
+      dfloat ex = dsplit(inv_fact(kExpTerms));
+      static_for<kExpTerms>([&](auto I) {
+        constexpr int k = kExpTerms - 1 - decltype(I)::value;
+        ex = fma(ex, x, dsplit(inv_fact(k)));
+      });
+      const dfloat e = row[kBoysK64] * ex;
+      const dfloat T2(2.0f * T.hi, 2.0f * T.lo);
+      static_for<L>([&](auto I) {
+        constexpr int n = L - 1 - decltype(I)::value;
+        F[n] = fma(T2, F[n + 1], e) * dsplit(inv_odd(n));
+      });
+    }
+  } else {
+    const dfloat rs = rsqrt_dfloat(T);
+    F[0] = dsplit(0.5 * kSqrtPi) * rs;
+    if constexpr (L > 0) {
+      const dfloat e(expf(-T.hi), 0.0f);
+      const dfloat rT = rs * rs;
+      const dfloat h(0.5f * rT.hi, 0.5f * rT.lo);
+      static_for<L>([&](auto I) {
+        constexpr int n = decltype(I)::value + 1;
+        F[n] = (dfloat(2 * n - 1) * F[n - 1] - e) * h;
+      });
+    }
+  }
+}
+
 template <typename Real>
 struct Boys;
 template <>
 struct Boys<double> {
-  static constexpr int K = kBoysK64, NROW = kBoysN64;
+  static constexpr int K = kBoysK64, NROW = kBoysN64, NCOL = K;
+  // table column staged in slot c (of NCOL) for class order L
+  static __host__ __device__ constexpr int col(int L, int c) { return L + c; }
   template <int L>
   static __device__ __forceinline__ void eval(double T, double (&F)[L + 1], const double* tabL, int stride,
                                               float /*t64*/) {
@@ -120,11 +181,25 @@ struct Boys<double> {
 };
 template <>
 struct Boys<float> {
-  static constexpr int K = kBoysK32, NROW = kBoysN32;
+  static constexpr int K = kBoysK32, NROW = kBoysN32, NCOL = K;
+  static __host__ __device__ constexpr int col(int L, int c) { return L + c; }
   template <int L>
   static __device__ __forceinline__ void eval(float T, float (&F)[L + 1], const float* tabL, int stride,
                                               float t64) {
     boys_fp32<L>(T, F, tabL, stride, t64);
+  }
+};
+
+template <>
+struct Boys<dfloat> {
+  // slots 0..K-1: F_{L..L+K-1}; slot K: e^{-T_i}, kept in the table's last
+  // column, which no class order reaches (L + K - 1 <= 15 < kBoysCols - 1)
+  static constexpr int K = kBoysK64, NROW = kBoysN64, NCOL = K + 1;
+  static __host__ __device__ constexpr int col(int L, int c) { return c < K ? L + c : kBoysCols - 1; }
+  template <int L>
+  static __device__ __forceinline__ void eval(dfloat T, dfloat (&F)[L + 1], const dfloat* tabL, int stride,
+                                              float /*t64*/) {
+    boys_dfloat<L>(T, F, tabL, stride);
   }
 };
 

@@ -41,6 +41,10 @@ template <>
 struct Vec4<float> {
   using type = float4;
 };
+template <>
+struct Vec4<dfloat> {
+  using type = dfloat4;
+};
 
 template <typename Real>
 struct PairView {
@@ -127,6 +131,8 @@ template <>
 __device__ __forceinline__ double rsqrt_r<double>(double x) { return rsqrt(x); }
 template <>
 __device__ __forceinline__ float rsqrt_r<float>(float x) { return rsqrtf(x); }
+template <>
+__device__ __forceinline__ dfloat rsqrt_r<dfloat>(dfloat x) { return rsqrt_dfloat(x); }
 
 // Chunk bookkeeping for the ket side: chunks of CS consecutive components, the
 // last one possibly shorter.
@@ -201,7 +207,7 @@ __device__ __forceinline__ void quartet_chunk(Real* __restrict__ so, const BraAt
         constexpr int nzoff = KC::off(c0);
         constexpr int NZ = KCh::nnz_of(CH);
 #pragma unroll
-        for (int z = 0; z < NZ; ++z) Ek[z] = __ldg(kp + (size_t)(4 + nzoff + z) * kstride);
+        for (int z = 0; z < NZ; ++z) Ek[z] = ldg_r(kp + (size_t)(4 + nzoff + z) * kstride);
         static_for<CS>([&](auto Cs) {
           constexpr int cs = decltype(Cs)::value;
           constexpr int c = c0 + cs;
@@ -256,9 +262,10 @@ __device__ __forceinline__ int find_bra(const int* __restrict__ prefix, int n, i
 //    The CTA stages the bra's primitive data and D block in shared memory,
 //    where every thread reads them as broadcasts, and reduces J_bra over the
 //    CTA (one FP64 add per element and item).
-//  * FP64 (kFlat true): a work item is a tile of consecutive quartets of the
-//    class pair's flattened (bra, screened ket) list, so tiles are full however
-//    few kets a bra has, and the loop has no barriers.  Each thread reads its
+//  * FP64 and double-float (kFlat true: 8-byte values): a work item is a tile
+//    of consecutive quartets of the class pair's flattened (bra, screened ket)
+//    list, so tiles are full however few kets a bra has, and the loop has no
+//    barriers.  Each thread reads its
 //    bra data through the L1 cache and reduces J_bra over the warp when the
 //    warp's quartets share one bra (else lane by lane).  At the FP64 rate the
 //    extra loads are free and the full tiles and missing barriers win (5-26 %
@@ -270,7 +277,7 @@ __device__ __forceinline__ int find_bra(const int* __restrict__ prefix, int n, i
 // symmetrises J = (J_acc + J_acc^T)/4 and K = (K_acc + K_acc^T)/8.
 template <typename Real>
 __host__ __device__ constexpr size_t jk_boys_smem() {
-  return (size_t)Boys<Real>::NROW * Boys<Real>::K * sizeof(Real);
+  return (size_t)Boys<Real>::NROW * Boys<Real>::NCOL * sizeof(Real);
 }
 
 template <typename Real>
@@ -294,7 +301,7 @@ __global__ void __launch_bounds__(kJKThreads) jk_kernel(JKParams<Real> P) {
   constexpr bool kFlat = jk_flat<Real>();
   constexpr int L = LA + LB + LC + LD;
   constexpr int NFB = 4 + BC::NNZ;
-  constexpr int BK = Boys<Real>::K, BR = Boys<Real>::NROW;
+  constexpr int BK = Boys<Real>::NCOL, BR = Boys<Real>::NROW;
   constexpr int NWARP = kJKThreads / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* sBoys = reinterpret_cast<Real*>(smem_raw);                     // [BR][BK]
@@ -305,7 +312,7 @@ __global__ void __launch_bounds__(kJKThreads) jk_kernel(JKParams<Real> P) {
   Real* sbra = sJw + NWARP * BC::NC;            // per-bra form: bra primitive data [pp][field]
 
   for (int x = threadIdx.x; x < BR * BK; x += blockDim.x)
-    sBoys[x] = P.boys[(x / BK) * kBoysCols + L + x % BK];
+    sBoys[x] = P.boys[(x / BK) * kBoysCols + Boys<Real>::col(L, x % BK)];
   __syncthreads();
   // thread = (chunk group cg, quartet q of the tile, bra-primitive subset bs);
   // the chunk group is the slowest index, so it is uniform within each warp
@@ -367,11 +374,11 @@ __global__ void __launch_bounds__(kJKThreads) jk_kernel(JKParams<Real> P) {
       const Real* bpd = M.bra.pd + i;
       const Real* Dbra = M.D + (size_t)bi.x * N + bi.y;
       auto bra = [&](int f, int pp) -> Real {
-        if constexpr (kFlat) return __ldg(bpd + (size_t)f * bstride + (size_t)pp * M.bra.n);
+        if constexpr (kFlat) return ldg_r(bpd + (size_t)f * bstride + (size_t)pp * M.bra.n);
         else return sbra[pp * NFB + f];
       };
       auto Dab = [&](int a) -> Real {
-        if constexpr (kFlat) return __ldg(Dbra + (size_t)(a / BC::NB) * N + a % BC::NB);
+        if constexpr (kFlat) return ldg_r(Dbra + (size_t)(a / BC::NB) * N + a % BC::NB);
         else return sDab[a];
       };
 #pragma unroll 1
@@ -436,7 +443,7 @@ __global__ void __launch_bounds__(kJKThreads) jk_kernel(JKParams<Real> P) {
           for (int a = 0; a < BC::NC; ++a) {
             Real v = jb[a * kJKThreads];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            for (int o = 16; o > 0; o >>= 1) v += shfl_xor_r(v, o);
             if (lane == 0) atomicAdd(&M.J[(size_t)(bi.x + a / BC::NB) * N + bi.y + a % BC::NB], (double)v);
           }
         }
@@ -454,7 +461,7 @@ __global__ void __launch_bounds__(kJKThreads) jk_kernel(JKParams<Real> P) {
       for (int a = 0; a < BC::NC; ++a) {
         Real v = jb[a * kJKThreads];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        for (int o = 16; o > 0; o >>= 1) v += shfl_xor_r(v, o);
         if (lane == 0) sJw[warp * BC::NC + a] = v;
       }
       __syncthreads();

@@ -32,30 +32,36 @@ int device_sm_count() {
   return n;
 }
 
+template <typename Real, int X, int Y>
+static cudaError_t launch_if(const JKParams<Real>& p, cudaStream_t s) {
+  if constexpr (std::is_same<Real, dfloat>::value && !dfloat_kernel(X, Y)) return cudaErrorInvalidValue;
+  else return launch_jk<Real, X, Y>(p, s);
+}
+
 template <typename Real>
 static cudaError_t dispatch_jk(int X, int Y, const JKParams<Real>& p, cudaStream_t s) {
   switch (X * 8 + Y) {
-    case 0: return launch_jk<Real, 0, 0>(p, s);
-    case 8: return launch_jk<Real, 1, 0>(p, s);
-    case 9: return launch_jk<Real, 1, 1>(p, s);
-    case 16: return launch_jk<Real, 2, 0>(p, s);
-    case 17: return launch_jk<Real, 2, 1>(p, s);
-    case 18: return launch_jk<Real, 2, 2>(p, s);
-    case 24: return launch_jk<Real, 3, 0>(p, s);
-    case 25: return launch_jk<Real, 3, 1>(p, s);
-    case 26: return launch_jk<Real, 3, 2>(p, s);
-    case 27: return launch_jk<Real, 3, 3>(p, s);
-    case 32: return launch_jk<Real, 4, 0>(p, s);
-    case 33: return launch_jk<Real, 4, 1>(p, s);
-    case 34: return launch_jk<Real, 4, 2>(p, s);
-    case 35: return launch_jk<Real, 4, 3>(p, s);
-    case 36: return launch_jk<Real, 4, 4>(p, s);
-    case 40: return launch_jk<Real, 5, 0>(p, s);
-    case 41: return launch_jk<Real, 5, 1>(p, s);
-    case 42: return launch_jk<Real, 5, 2>(p, s);
-    case 43: return launch_jk<Real, 5, 3>(p, s);
-    case 44: return launch_jk<Real, 5, 4>(p, s);
-    case 45: return launch_jk<Real, 5, 5>(p, s);
+    case 0: return launch_if<Real, 0, 0>(p, s);
+    case 8: return launch_if<Real, 1, 0>(p, s);
+    case 9: return launch_if<Real, 1, 1>(p, s);
+    case 16: return launch_if<Real, 2, 0>(p, s);
+    case 17: return launch_if<Real, 2, 1>(p, s);
+    case 18: return launch_if<Real, 2, 2>(p, s);
+    case 24: return launch_if<Real, 3, 0>(p, s);
+    case 25: return launch_if<Real, 3, 1>(p, s);
+    case 26: return launch_if<Real, 3, 2>(p, s);
+    case 27: return launch_if<Real, 3, 3>(p, s);
+    case 32: return launch_if<Real, 4, 0>(p, s);
+    case 33: return launch_if<Real, 4, 1>(p, s);
+    case 34: return launch_if<Real, 4, 2>(p, s);
+    case 35: return launch_if<Real, 4, 3>(p, s);
+    case 36: return launch_if<Real, 4, 4>(p, s);
+    case 40: return launch_if<Real, 5, 0>(p, s);
+    case 41: return launch_if<Real, 5, 1>(p, s);
+    case 42: return launch_if<Real, 5, 2>(p, s);
+    case 43: return launch_if<Real, 5, 3>(p, s);
+    case 44: return launch_if<Real, 5, 4>(p, s);
+    case 45: return launch_if<Real, 5, 5>(p, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -194,12 +200,13 @@ int get_plan(fsim_basis* b, double tau, int shard, int nshards, int precision, F
           const long long target = (long long)device_sm_count() * 2 * kJKThreads;
           for (int c : {3, 9})
             if (cp.nquartets * ps < target && c <= CX.ppmax) ps = c;
-          const int nch = precision == FSIM_FP64 ? jk_chunks<double>(X, Y) : jk_chunks<float>(X, Y);
+          const int nch = jk_chunks_precision(precision, X, Y);
           for (int c : {2, 4})
             if (cp.nquartets * ps * cs < target && c <= nch) cs = c;
         }
       }
       FSIM_TRY(set_class_plan(b, X, Y, count, ps, coop, cp, cs, jk_flat_precision(precision)));
+      cp.fp64 = precision == FSIM_DFLOAT && !dfloat_default(X, Y);
       P->nquartets += cp.nquartets;
     }
   *out = P;
@@ -230,30 +237,39 @@ int ensure_scratch(fsim_basis* b) {
 
 // One class pair's launch with the shape its plan entry holds; J/K
 // accumulators passed in (the basis's own or caller-supplied scratch).
+// D64: the FP64 density, which a double-float build passes for the class pairs
+// it evaluates with the FP64 kernel.
 template <typename Real>
 static cudaError_t launch_cp(fsim_basis* b, int X, int Y, const ClassPairPlan& cp, const Real* Dr, double* Jacc,
-                             double* Kacc, float boys64_T, cudaStream_t s) {
-  const Real* boys = std::is_same<Real, double>::value ? (const Real*)b->d_boys64 : (const Real*)b->d_boys32;
+                             double* Kacc, float boys64_T, cudaStream_t s, const double* D64 = nullptr) {
+  if constexpr (std::is_same<Real, dfloat>::value) {
+    if (!dfloat_kernel(X, Y) || cp.fp64) return launch_cp<double>(b, X, Y, cp, D64, Jacc, Kacc, boys64_T, s);
+  }
+  const Real* boys = std::is_same<Real, double>::value   ? (const Real*)b->d_boys64
+                     : std::is_same<Real, float>::value  ? (const Real*)b->d_boys32
+                                                         : (const Real*)b->d_boysx;
   if (cp.nitems == 0) return cudaSuccess;
-  if (cp.coop) {
-    CoopParams<Real> p{};
-    p.bra = b->cls[X].view<Real>();
-    p.ket = b->cls[Y].view<Real>();
-    make_cls_desc(X, p.bd);
-    make_cls_desc(Y, p.kd);
-    p.same = X == Y ? 1 : 0;
-    p.list_mode = 0;
-    p.tile_prefix = cp.d_prefix;
-    p.ket_count = cp.d_count;
-    p.tq = cp.tq;
-    p.nitems = cp.nitems;
-    p.N = b->nbf;
-    p.D = Dr;
-    p.J = Jacc;
-    p.K = Kacc;
-    p.boys = boys;
-    p.boys64_T = boys64_T;
-    return launch_coop<Real>(p, cp.nitems, s);
+  if constexpr (!std::is_same<Real, dfloat>::value) {  // the cooperative kernel exists in FP32 and FP64
+    if (cp.coop) {
+      CoopParams<Real> p{};
+      p.bra = b->cls[X].view<Real>();
+      p.ket = b->cls[Y].view<Real>();
+      make_cls_desc(X, p.bd);
+      make_cls_desc(Y, p.kd);
+      p.same = X == Y ? 1 : 0;
+      p.list_mode = 0;
+      p.tile_prefix = cp.d_prefix;
+      p.ket_count = cp.d_count;
+      p.tq = cp.tq;
+      p.nitems = cp.nitems;
+      p.N = b->nbf;
+      p.D = Dr;
+      p.J = Jacc;
+      p.K = Kacc;
+      p.boys = boys;
+      p.boys64_T = boys64_T;
+      return launch_coop<Real>(p, cp.nitems, s);
+    }
   }
   JKParams<Real> p{};
   p.one = JKMol<Real>{b->cls[X].view<Real>(), b->cls[Y].view<Real>(), cp.d_prefix, cp.d_count, b->nbf, Dr, Jacc, Kacc};
@@ -295,7 +311,8 @@ static int ensure_aux_streams(fsim_basis* b) {
 // fork and a join event on s, so that the short launches and the tails of the
 // long ones overlap.  All launches add into the same accumulators (atomics).
 template <typename Real>
-static int launch_all(fsim_basis* b, FockPlan* plan, const Real* Dr, float boys64_T, bool timing, cudaStream_t s) {
+static int launch_all(fsim_basis* b, FockPlan* plan, const Real* Dr, float boys64_T, bool timing, cudaStream_t s,
+                      const double* D64 = nullptr) {
   if (!timing) {
     FSIM_TRY(ensure_aux_streams(b));
     struct Job {
@@ -326,7 +343,7 @@ static int launch_all(fsim_basis* b, FockPlan* plan, const Real* Dr, float boys6
       load[k] += j.cost;
       ++b->last_launches;
       const cudaError_t e = launch_cp<Real>(b, j.X, j.Y, plan->cp[j.X][j.Y], Dr, b->d_Jacc, b->d_Kacc, boys64_T,
-                                            st[k]);
+                                            st[k], D64);
       if (e != cudaSuccess) {
         set_error("J/K kernel (%d|%d): %s", j.X, j.Y, cudaGetErrorString(e));
         return FSIM_ECUDA;
@@ -347,7 +364,7 @@ static int launch_all(fsim_basis* b, FockPlan* plan, const Real* Dr, float boys6
       if (cp.nitems == 0) continue;
       ++b->last_launches;
       if (timing) FSIM_CK(cudaEventRecord(b->ev[ci][0], s));
-      const cudaError_t e = launch_cp<Real>(b, X, Y, cp, Dr, b->d_Jacc, b->d_Kacc, boys64_T, s);
+      const cudaError_t e = launch_cp<Real>(b, X, Y, cp, Dr, b->d_Jacc, b->d_Kacc, boys64_T, s, D64);
       if (e != cudaSuccess) {
         set_error("J/K kernel (%d|%d): %s", X, Y, cudaGetErrorString(e));
         return FSIM_ECUDA;
@@ -358,8 +375,8 @@ static int launch_all(fsim_basis* b, FockPlan* plan, const Real* Dr, float boys6
 }
 
 int fock_build_device(fsim_basis* b, const double* dD, double* dJ, double* dK, const fsim_fock_opts& o) {
-  if (o.precision != FSIM_FP64 && o.precision != FSIM_MIXED) {
-    set_error("fsim_fock_build: precision must be FSIM_FP64 or FSIM_MIXED");
+  if (o.precision != FSIM_FP64 && o.precision != FSIM_MIXED && o.precision != FSIM_DFLOAT) {
+    set_error("fsim_fock_build: precision must be FSIM_FP64, FSIM_MIXED or FSIM_DFLOAT");
     return FSIM_EINVAL;
   }
   if (o.nshards < 1 || o.shard < 0 || o.shard >= o.nshards || !(o.schwarz_tau >= 0.0)) {
@@ -374,6 +391,7 @@ int fock_build_device(fsim_basis* b, const double* dD, double* dJ, double* dK, c
   cudaStream_t s = (cudaStream_t)o.stream;
   FSIM_TRY(ensure_schwarz(b));
   FSIM_TRY(ensure_scratch(b));
+  if (o.precision == FSIM_DFLOAT) FSIM_TRY(ensure_dfloat(b));
   FockPlan* plan = nullptr;
   FSIM_TRY(get_plan(b, o.schwarz_tau, o.shard, o.nshards, o.precision, &plan, 0));
   const int N = b->nbf;
@@ -394,6 +412,11 @@ int fock_build_device(fsim_basis* b, const double* dD, double* dJ, double* dK, c
     FSIM_CK(cudaGetLastError());
     ++b->last_launches;
     FSIM_TRY(launch_all<float>(b, plan, b->d_D32, b64, o.timing != 0, s));
+  } else if (o.precision == FSIM_DFLOAT) {
+    launch_split(dD, b->d_Dx, n2, s);
+    FSIM_CK(cudaGetLastError());
+    ++b->last_launches;
+    FSIM_TRY(launch_all<dfloat>(b, plan, b->d_Dx, b64, o.timing != 0, s, dD));
   } else {
     FSIM_TRY(launch_all<double>(b, plan, dD, b64, o.timing != 0, s));
   }
@@ -693,7 +716,7 @@ namespace fsim {
 
 template <typename Real>
 static int autotune_impl(fsim_basis* b, FockPlan* plan, const Real* Dr, float b64, cudaStream_t s, int* choice,
-                         float* best_ms) {
+                         float* best_ms, const double* D64 = nullptr) {
   cudaEvent_t e0, e1;
   FSIM_CK(cudaEventCreate(&e0));
   FSIM_CK(cudaEventCreate(&e1));
@@ -706,25 +729,30 @@ static int autotune_impl(fsim_basis* b, FockPlan* plan, const Real* Dr, float b6
       std::vector<int> count;
       screened_counts(b, X, Y, plan->tau, plan->shard, plan->nshards, count);
       struct Cand {
-        int psplit, coop, csplit;
+        int psplit, coop, csplit, fp64;
       };
       std::vector<Cand> cands;
       const int nch = jk_chunks<Real>(X, Y);
-      for (int ps : {1, 3, 9})
-        for (int cs : {1, 2, 4})
-          if (ps <= b->cls[X].ppmax && cs <= nch) cands.push_back({ps, 0, cs});
-      cands.push_back({1, 1, 1});
+      constexpr bool kDf = std::is_same<Real, dfloat>::value;
+      // double-float builds: each shape with the double-float and with the FP64 kernel
+      const int f64_lo = kDf && !dfloat_kernel(X, Y) ? 1 : 0, f64_hi = kDf ? 1 : 0;
+      for (int f64 = f64_lo; f64 <= f64_hi; ++f64)
+        for (int ps : {1, 3, 9})
+          for (int cs : {1, 2, 4})
+            if (ps <= b->cls[X].ppmax && cs <= nch) cands.push_back({ps, 0, cs, f64});
+      if (!kDf) cands.push_back({1, 1, 1, 0});
       float best = 1e30f;
       Cand win = cands[0];
       ClassPairPlan tmp;
       for (const Cand& c : cands) {
         if ((rc = set_class_plan(b, X, Y, count, c.psplit, c.coop, tmp, c.csplit, jk_flat<Real>())) != FSIM_OK)
           break;
+        tmp.fp64 = c.fp64;
         float t[3];
-        cudaError_t e = launch_cp<Real>(b, X, Y, tmp, Dr, b->d_Jacc, b->d_Kacc, b64, s);  // warm-up
+        cudaError_t e = launch_cp<Real>(b, X, Y, tmp, Dr, b->d_Jacc, b->d_Kacc, b64, s, D64);  // warm-up
         for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
           cudaEventRecord(e0, s);
-          e = launch_cp<Real>(b, X, Y, tmp, Dr, b->d_Jacc, b->d_Kacc, b64, s);
+          e = launch_cp<Real>(b, X, Y, tmp, Dr, b->d_Jacc, b->d_Kacc, b64, s, D64);
           cudaEventRecord(e1, s);
           cudaEventSynchronize(e1);
           cudaEventElapsedTime(&t[r], e0, e1);
@@ -744,7 +772,8 @@ static int autotune_impl(fsim_basis* b, FockPlan* plan, const Real* Dr, float b6
       dev_free(tmp.d_count);
       if (rc != FSIM_OK) break;
       rc = set_class_plan(b, X, Y, count, win.psplit, win.coop, cp, win.csplit, jk_flat<Real>());
-      if (choice) choice[ci] = win.coop ? -1 : 10 * win.psplit + win.csplit;
+      cp.fp64 = win.fp64;
+      if (choice) choice[ci] = win.coop ? -1 : 10 * win.psplit + win.csplit + 100 * win.fp64;
       if (best_ms) best_ms[ci] = best;
     }
   cudaEventDestroy(e0);
@@ -755,13 +784,50 @@ static int autotune_impl(fsim_basis* b, FockPlan* plan, const Real* Dr, float b6
 
 }  // namespace fsim
 
+extern "C" int fsim_set_launch(fsim_basis* b, const fsim_fock_opts* opts, const int* choice) {
+  if (!b || !opts || !choice) {
+    set_error("fsim_set_launch: null pointer");
+    return FSIM_EINVAL;
+  }
+  const fsim_fock_opts& o = *opts;
+  if (o.precision != FSIM_FP64 && o.precision != FSIM_MIXED && o.precision != FSIM_DFLOAT) {
+    set_error("fsim_set_launch: bad precision");
+    return FSIM_EINVAL;
+  }
+  FSIM_TRY(ensure_schwarz(b));
+  FockPlan* plan = nullptr;
+  FSIM_TRY(get_plan(b, o.schwarz_tau, o.shard, o.nshards, o.precision, &plan, 0));
+  const bool df = o.precision == FSIM_DFLOAT;
+  for (int X = 0; X < kNumPairCls; ++X)
+    for (int Y = 0; Y <= X; ++Y) {
+      const int c = choice[X * kNumPairCls + Y];
+      ClassPairPlan& cp = plan->cp[X][Y];
+      if (c == 0 || cp.nquartets == 0) continue;
+      const int coop = c == -1 ? 1 : 0;
+      const int f64 = c >= 100 ? 1 : 0, ps = coop ? 1 : (c % 100) / 10, cs = coop ? 1 : c % 10;
+      const bool ok = c >= -1 && c < 200 && (coop ? !df : ((ps == 1 || ps == 3 || ps == 9) && ps <= b->cls[X].ppmax &&
+                                                          (cs == 1 || cs == 2 || cs == 4) &&
+                                                          cs <= jk_chunks_precision(o.precision, X, Y))) &&
+                      (!f64 || df) && (!df || f64 || dfloat_kernel(X, Y));
+      if (!ok) {
+        set_error("fsim_set_launch: choice %d not valid for class pair (%d|%d) in precision %d", c, X, Y, o.precision);
+        return FSIM_EINVAL;
+      }
+      std::vector<int> count;
+      screened_counts(b, X, Y, plan->tau, plan->shard, plan->nshards, count);
+      FSIM_TRY(set_class_plan(b, X, Y, count, ps, coop, cp, cs, jk_flat_precision(o.precision)));
+      cp.fp64 = df && (f64 || !dfloat_kernel(X, Y));
+    }
+  return FSIM_OK;
+}
+
 extern "C" int fsim_autotune(fsim_basis* b, const fsim_fock_opts* opts, int* choice, float* best_ms) {
   if (!b || !opts) {
     set_error("fsim_autotune: null pointer");
     return FSIM_EINVAL;
   }
   const fsim_fock_opts& o = *opts;
-  if (o.precision != FSIM_FP64 && o.precision != FSIM_MIXED) {
+  if (o.precision != FSIM_FP64 && o.precision != FSIM_MIXED && o.precision != FSIM_DFLOAT) {
     set_error("fsim_autotune: bad precision");
     return FSIM_EINVAL;
   }
@@ -771,6 +837,7 @@ extern "C" int fsim_autotune(fsim_basis* b, const fsim_fock_opts* opts, int* cho
     for (int i = 0; i < 36; ++i) best_ms[i] = -1.0f;
   FSIM_TRY(ensure_schwarz(b));
   FSIM_TRY(ensure_scratch(b));
+  if (o.precision == FSIM_DFLOAT) FSIM_TRY(ensure_dfloat(b));
   FockPlan* plan = nullptr;
   FSIM_TRY(get_plan(b, o.schwarz_tau, o.shard, o.nshards, o.precision, &plan, 0));
   cudaStream_t s = (cudaStream_t)o.stream;
@@ -779,6 +846,11 @@ extern "C" int fsim_autotune(fsim_basis* b, const fsim_fock_opts* opts, int* cho
   if (o.precision == FSIM_MIXED) {
     FSIM_CK(cudaMemsetAsync(b->d_D32, 0, n2 * sizeof(float), s));
     return autotune_impl<float>(b, plan, b->d_D32, b64, s, choice, best_ms);
+  }
+  if (o.precision == FSIM_DFLOAT) {
+    // zero bytes: also a zero FP64 density of the same size for the FP64-evaluated class pairs
+    FSIM_CK(cudaMemsetAsync(b->d_Dx, 0, n2 * sizeof(dfloat), s));
+    return autotune_impl<dfloat>(b, plan, b->d_Dx, b64, s, choice, best_ms, reinterpret_cast<const double*>(b->d_Dx));
   }
   double* Dz = nullptr;
   FSIM_TRY(dev_alloc(&Dz, n2));

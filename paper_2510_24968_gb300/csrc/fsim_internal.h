@@ -61,6 +61,8 @@ struct DevClass {
   float* pd32 = nullptr;
   double4_32a* pq64 = nullptr;  // (p, P) at [ppmax][n]
   float4* pq32 = nullptr;
+  dfloat* pdx = nullptr;    // double-float copies of pd64 / pq64 (made on first FSIM_DFLOAT use)
+  dfloat4* pqx = nullptr;
   std::vector<int4> h_idx;  // host copy, same order
   std::vector<int> h_npp;
   std::vector<double> h_Q;  // Schwarz bound of each pair, same order
@@ -76,6 +78,10 @@ inline PairView<double> DevClass::view<double>() const {
 template <>
 inline PairView<float> DevClass::view<float>() const {
   return PairView<float>{n, ppmax, idx, npp, pd32, pq32};
+}
+template <>
+inline PairView<dfloat> DevClass::view<dfloat>() const {
+  return PairView<dfloat>{n, ppmax, idx, npp, pdx, pqx};
 }
 
 // Ket components per register chunk.  The per-thread registers of the unrolled
@@ -139,6 +145,20 @@ __host__ __device__ constexpr int chunk_size(int X, int Y) {
   return 1;
 }
 
+// Class pairs that have a double-float kernel: all but (dd|dp) and (dd|dd),
+// whose fully unrolled double-float code takes minutes to compile and spills
+// far more than the FP64 kernel; FSIM_DFLOAT builds run those two in FP64.
+__host__ __device__ constexpr bool dfloat_kernel(int X, int Y) { return !(X == 5 && Y >= 4); }
+// Default kernel of a class pair in an FSIM_DFLOAT build (the autotuner times
+// both): double-float up to total angular momentum 4, where the Boys function
+// and the prologue weigh most (measured on (H2O)_8: 3-8x faster than FP64);
+// FP64 from 5, where the contraction's dependent double-float chains at 255
+// registers leave the FP32 pipe latency-bound and the two kernels run even.
+__host__ __device__ constexpr bool dfloat_default(int X, int Y) {
+  return dfloat_kernel(X, Y) && pair_cls_la(X) + pair_cls_lb(X) + pair_cls_la(Y) + pair_cls_lb(Y) <= 4;
+}
+static_assert(sizeof(dfloat) == sizeof(double), "double-float values share the FP64 layouts and chunk sizes");
+
 // Ket chunks of the unrolled kernel for a class pair (host side of KetChunks).
 template <typename Real>
 __host__ __device__ constexpr int jk_chunks(int X, int Y) {
@@ -153,6 +173,7 @@ struct ClassPairPlan {
   int psplit = 1;
   int csplit = 1;           // ket chunk groups per CTA (unrolled kernel)
   int coop = 0;             // 1: warp-cooperative table-driven kernel
+  int fp64 = 0;             // FSIM_DFLOAT plans: 1 = this class pair runs the FP64 kernel
   int tq = kJKThreads;      // kets per work item
   int* d_prefix = nullptr;  // [nbra + 1]
   int* d_count = nullptr;   // [nbra]
@@ -212,6 +233,8 @@ struct fsim_basis {
   std::vector<double> Q;  // nshell x nshell
   double* d_boys64 = nullptr;
   float* d_boys32 = nullptr;
+  fsim::dfloat* d_boysx = nullptr;  // double-float copy of the FP64 table (first FSIM_DFLOAT use)
+  bool dfloat_ready = false;
   std::vector<fsim::FockPlan*> plans;
   long long last_quartets = 0;
   // scratch
@@ -221,6 +244,7 @@ struct fsim_basis {
   double* d_J = nullptr;
   double* d_K = nullptr;
   float* d_D32 = nullptr;
+  fsim::dfloat* d_Dx = nullptr;  // double-float density copy
   // per class-pair timing of the last build
   cudaEvent_t ev[fsim::kNumPairCls * fsim::kNumPairCls][2] = {};
   bool ev_ok = false;
@@ -241,7 +265,17 @@ int get_plan(fsim_basis* b, double tau, int shard, int nshards, int precision, F
 int set_class_plan(fsim_basis* b, int X, int Y, const std::vector<int>& count, int psplit, int coop,
                    ClassPairPlan& cp, int csplit, int flat);
 // the unrolled kernel's work decomposition of a precision (see jk_kernel)
-inline int jk_flat_precision(int precision) { return precision == FSIM_FP64 ? (int)jk_flat<double>() : (int)jk_flat<float>(); }
+inline int jk_flat_precision(int precision) {
+  return precision == FSIM_MIXED ? (int)jk_flat<float>() : (int)jk_flat<double>();  // dfloat: as FP64
+}
+// ket chunks of a class pair in the precision's kernel
+inline int jk_chunks_precision(int precision, int X, int Y) {
+  return precision == FSIM_MIXED ? jk_chunks<float>(X, Y) : jk_chunks<double>(X, Y);  // dfloat: as FP64
+}
+// double-float pair data, Boys table and density buffer (allocated on first use)
+int ensure_dfloat(fsim_basis* b);
+// out[i] = nearest dfloat of in[i]
+void launch_split(const double* in, dfloat* out, size_t n, cudaStream_t s);
 int ensure_scratch(fsim_basis* b);
 int ensure_schwarz(fsim_basis* b);
 int device_sm_count();

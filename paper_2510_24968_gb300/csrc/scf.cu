@@ -9,8 +9,9 @@
 // Mixed precision (FSIM_MIXED): Fock builds with FP32 integrals and FP64
 // accumulation.  With `incremental`, G(D_n) = G(D_{n-1}) + G(D_n - D_{n-1}),
 // so the FP32 error scales with the density change; with `final_fp64`, once
-// the mixed iteration has settled (|dE| < 1e-7) one full FP64 build resets G
-// and the iteration continues incrementally to the requested thresholds.
+// the mixed iteration has settled (|dE| < 1e-7) one full FP64-accurate build
+// (FP64, or double-float with final_fp64 == 2) resets G and the iteration
+// continues incrementally to the requested thresholds.
 #include <cublas_v2.h>
 #include <cusolverDn.h>
 
@@ -234,8 +235,10 @@ int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res) {
   const fsim_scf_opts& o = *opts;
   const int N = b->nbf_ext();
   if (o.nelec <= 0 || (o.nelec & 1) || o.nelec / 2 > N || o.max_iter < 1 || o.diis_size < 0 ||
-      (o.guess == FSIM_GUESS_DENSITY && !o.D0) || (o.guess != FSIM_GUESS_CORE && o.guess != FSIM_GUESS_DENSITY)) {
-    set_error("fsim_scf: bad options (nelec %d must be even and <= 2 nbf, max_iter %d)", o.nelec, o.max_iter);
+      (o.guess == FSIM_GUESS_DENSITY && !o.D0) || (o.guess != FSIM_GUESS_CORE && o.guess != FSIM_GUESS_DENSITY) ||
+      o.final_fp64 < 0 || o.final_fp64 > 2) {
+    set_error("fsim_scf: bad options (nelec %d must be even and <= 2 nbf, max_iter %d, final_fp64 %d in 0..2)",
+              o.nelec, o.max_iter, o.final_fp64);
     return FSIM_EINVAL;
   }
   const auto t_start = std::chrono::steady_clock::now();
@@ -346,6 +349,9 @@ int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res) {
   fsim_fock_opts fo = o.fock;
   fo.ptr_mode = FSIM_PTR_DEVICE;
   const bool mixed = o.fock.precision == FSIM_MIXED;
+  // precision of the FP64-accurate builds: the requested one, or on the mixed
+  // path the resets' (FP64, or double-float with final_fp64 == 2)
+  const int prec64 = !mixed ? o.fock.precision : (o.final_fp64 == 2 ? FSIM_DFLOAT : FSIM_FP64);
   // phase 0: mixed settling; phase 2: final accuracy.  With final_fp64 each
   // FP64 build resets G; the iteration only stops once the density has not
   // moved (rms 1e-6) since the last reset, so the FP32 part of G is tiny.
@@ -366,7 +372,7 @@ int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res) {
   for (it = 1; it <= o.max_iter; ++it) {
     // ---- G(D), full or incremental
     const bool want64 = !mixed || (phase == 2 && o.final_fp64 && !have_G);
-    fo.precision = want64 ? FSIM_FP64 : FSIM_MIXED;
+    fo.precision = want64 ? prec64 : FSIM_MIXED;
     if (o.incremental && have_G && !want64) {
       add_kernel<<<bl, th, 0, c.s>>>(D, Dn, -1.0, dD, n2);  // dD = D - D_prev (Dn holds D_prev)
       FSIM_TRY(fock_build_ext_device(b, dD, J, K, fo));

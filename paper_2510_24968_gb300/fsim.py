@@ -24,6 +24,7 @@ FSIM_EDEVICE_TIMEOUT = -5
 FSIM_ENOMEM = -6
 FSIM_FP64 = 0
 FSIM_MIXED = 1
+FSIM_DFLOAT = 2
 FSIM_BASIS_SPHERICAL = 1
 FSIM_PTR_HOST = 0
 FSIM_PTR_DEVICE = 1
@@ -34,7 +35,7 @@ FSIM_GUESS_DENSITY = 1
 EXPORTS = ["fsim_basis_create", "fsim_basis_create_ex", "fsim_basis_destroy", "fsim_basis_nbf",
            "fsim_basis_nbf_cart", "fsim_basis_nshell",
            "fsim_basis_pair_counts", "fsim_enuc", "fsim_onee", "fsim_schwarz", "fsim_fock_opts_default",
-           "fsim_fock_build", "fsim_fock_build_noalloc", "fsim_autotune", "fsim_last_quartet_count", "fsim_last_class_times", "fsim_eri_quartets", "fsim_eri_dump",
+           "fsim_fock_build", "fsim_fock_build_noalloc", "fsim_autotune", "fsim_set_launch", "fsim_last_quartet_count", "fsim_last_class_times", "fsim_eri_quartets", "fsim_eri_dump",
            "fsim_scf_opts_default", "fsim_scf", "fsim_batch_create", "fsim_batch_fock", "fsim_batch_destroy",
            "fsim_scf_batched", "fsim_guess_layout", "fsim_guess_features", "fsim_guess_targets",
            "fsim_guess_assemble", "fsim_mlp_create", "fsim_mlp_destroy", "fsim_mlp_nparams", "fsim_mlp_params",
@@ -106,6 +107,7 @@ def load():
     L.fsim_fock_build.argtypes = [vp, vp, vp, vp, C.POINTER(fsim_fock_opts)]
     L.fsim_fock_build_noalloc.argtypes = [vp, vp, vp, vp, C.POINTER(fsim_fock_opts)]
     L.fsim_autotune.argtypes = [vp, C.POINTER(fsim_fock_opts), ip, C.POINTER(C.c_float)]
+    L.fsim_set_launch.argtypes = [vp, C.POINTER(fsim_fock_opts), ip]
     L.fsim_last_quartet_count.argtypes = [vp]
     L.fsim_last_quartet_count.restype = C.c_longlong
     L.fsim_last_class_times.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_longlong), ip]
@@ -261,6 +263,15 @@ class Basis:
         ms = (C.c_float * 36)()
         _check(load().fsim_autotune(self.h, C.byref(o), ch, ms))
         return {(i // 6, i % 6): (ch[i], ms[i]) for i in range(36) if ch[i] != 0}
+
+    def set_launch(self, choices, tau=1e-10, precision=FSIM_MIXED, shard=0, nshards=1):
+        """Launch shapes {(X, Y): choice} in fsim_autotune's encoding (e.g. a saved tuning)."""
+        o = fsim_fock_opts_default()
+        o.schwarz_tau, o.precision, o.shard, o.nshards = tau, precision, shard, nshards
+        ch = (C.c_int * 36)()
+        for (x, y), c in choices.items():
+            ch[x * 6 + y] = int(c)
+        _check(load().fsim_set_launch(self.h, C.byref(o), ch))
 
     def last_quartet_count(self) -> int:
         return load().fsim_last_quartet_count(self.h)

@@ -18,7 +18,7 @@ import numpy as np
 
 from fsim_synth import workload
 
-from .fsim import FSIM_FP64, FSIM_MIXED, Basis
+from .fsim import FSIM_DFLOAT, FSIM_FP64, FSIM_MIXED, Basis
 
 _NAMES = ["ss", "ps", "pp", "ds", "dp", "dd"]
 
@@ -29,7 +29,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--workload", default="water8")
     ap.add_argument("--tau", type=float, default=1e-10)
-    ap.add_argument("--precision", choices=["mixed", "fp64", "both"], default="mixed")
+    ap.add_argument("--precision", choices=["mixed", "fp64", "dfloat", "both", "all"], default="mixed")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--tune", action="store_true", help="autotune launch shapes first")
     ap.add_argument("--boys-fp64-T", type=float, default=0.0)
@@ -49,9 +49,10 @@ def main(argv=None):
     Dn = np.random.default_rng(0).standard_normal((N, N)) * 0.02
     D = torch.from_numpy(Dn + Dn.T).cuda()
     J, K = torch.zeros_like(D), torch.zeros_like(D)
-    precs = {"mixed": [FSIM_MIXED], "fp64": [FSIM_FP64], "both": [FSIM_MIXED, FSIM_FP64]}[a.precision]
+    precs = {"mixed": [FSIM_MIXED], "fp64": [FSIM_FP64], "dfloat": [FSIM_DFLOAT], "both": [FSIM_MIXED, FSIM_FP64],
+             "all": [FSIM_MIXED, FSIM_FP64, FSIM_DFLOAT]}[a.precision]
     for prec in precs:
-        name = "mixed" if prec == FSIM_MIXED else "fp64"
+        name = {FSIM_MIXED: "mixed", FSIM_FP64: "fp64", FSIM_DFLOAT: "dfloat"}[prec]
         kw = dict(tau=a.tau, precision=prec, boys_fp64_T=a.boys_fp64_T)
         if a.tune:
             tuned = gb.autotune(tau=a.tau, precision=prec)
