@@ -352,8 +352,12 @@ def run_ours(args):
         rmx = gb.scf(precision=FSIM_MIXED, tau=args.tau, stream=sptr)
         # mixed with double-float resets (FP64-accurate builds on the FP32 pipe)
         rdf = gb.scf(precision=FSIM_MIXED, tau=args.tau, stream=sptr, final_fp64=2)
+        # every build FP64-accurate, in the autotuned double-float/FP64 kernel mix
+        rdd = gb.scf(precision=FSIM_DFLOAT, tau=args.tau, stream=sptr)
         tte = {"fp64_s": time_to_energy(r64, r64["e_total"]), "mixed_s": time_to_energy(rmx, r64["e_total"]),
                "mixed_dfloat_resets_s": time_to_energy(rdf, r64["e_total"]),
+               "dfloat_s": time_to_energy(rdd, r64["e_total"]), "dfloat_iters": rdd["iters"],
+               "dfloat_vs_fp64_eh": rdd["e_total"] - r64["e_total"],
                "fp64_iters": r64["iters"], "mixed_iters": rmx["iters"], "mixed_fp64_builds": rmx["fp64_builds"],
                "mixed_dfloat_resets_iters": rdf["iters"], "mixed_dfloat_resets_builds": rdf["fp64_builds"],
                "mixed_vs_fp64_eh": rmx["e_total"] - r64["e_total"],
@@ -365,6 +369,7 @@ def run_ours(args):
             tte["fp64_vs_oracle_eh"] = r64["e_total"] - g["e_total"]
             tte["mixed_vs_oracle_eh"] = rmx["e_total"] - g["e_total"]
             tte["mixed_dfloat_resets_vs_oracle_eh"] = rdf["e_total"] - g["e_total"]
+            tte["dfloat_vs_oracle_eh"] = rdd["e_total"] - g["e_total"]
         if tte["fp64_s"] and tte["mixed_s"]:
             tte["speedup"] = tte["fp64_s"] / tte["mixed_s"]
         if tte["fp64_s"] and tte["mixed_dfloat_resets_s"]:

@@ -298,8 +298,8 @@ void fsim_batch_destroy(fsim_batch* batch);
  * per iteration one batched Fock build (graph replay; FP64 and/or mixed
  * group as each molecule's state requires) and the per-molecule FP64 linear
  * algebra spread over several streams; converged molecules drop out.  Same
- * options and per-molecule semantics as fsim_scf (core-H guess only; each
- * molecule's electron count is its nuclear charge).  results: nmol entries;
+ * options and per-molecule semantics as fsim_scf (core-H guess only; FSIM_FP64
+ * or FSIM_MIXED; each molecule's electron count is its nuclear charge).  results: nmol entries;
  * time_s is the time from the start of the iteration loop (after the set-up:
  * one-electron matrices, orthogonaliser, guess, batch plans) at which that
  * molecule converged; t_hist counts from the same point.

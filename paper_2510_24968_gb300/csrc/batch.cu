@@ -442,8 +442,9 @@ extern "C" int fsim_scf_batched(fsim_basis* const* bases, int nmol, const fsim_s
   const fsim_scf_opts& o = *opts;
   const bool mixed = o.fock.precision == FSIM_MIXED;
   const int md = o.diis_size;
-  if (o.max_iter < 1 || md < 0 || md > 16 || o.guess != FSIM_GUESS_CORE) {
-    set_error("fsim_scf_batched: bad options (core guess only, diis_size <= 16)");
+  if (o.max_iter < 1 || md < 0 || md > 16 || o.guess != FSIM_GUESS_CORE ||
+      (o.fock.precision != FSIM_FP64 && o.fock.precision != FSIM_MIXED)) {
+    set_error("fsim_scf_batched: bad options (core guess only, diis_size <= 16, FSIM_FP64 or FSIM_MIXED)");
     return FSIM_EINVAL;
   }
   const auto t0 = std::chrono::steady_clock::now();

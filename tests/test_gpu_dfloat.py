@@ -157,7 +157,16 @@ def test_scf_mixed_with_dfloat_resets_full_size_cluster():
     assert abs(r["e_total"] - gold["e_total"]) < 1e-8
 
 
-def test_dfloat_bad_reset_option_rejected():
-    from paper_2510_24968_gb300 import FSIM_MIXED, Basis, FsimError
+def test_dfloat_bad_options_rejected():
+    # an unknown reset mode; the batched paths, which have FP64 and mixed builds only
+    from paper_2510_24968_gb300 import FSIM_DFLOAT, FSIM_MIXED, Basis, Batch, FsimError, scf_batched
+    gb = Basis(workload("water"))
     with pytest.raises(FsimError):
-        Basis(workload("water")).scf(precision=FSIM_MIXED, tau=0.0, final_fp64=3)
+        gb.scf(precision=FSIM_MIXED, tau=0.0, final_fp64=3)
+    with pytest.raises(FsimError):
+        scf_batched([gb], precision=FSIM_DFLOAT, tau=1e-10, max_iter=2)
+    D = torch.zeros((gb.nbf, gb.nbf), dtype=torch.float64, device="cuda")
+    bt = Batch([gb], [D], [torch.zeros_like(D)], [torch.zeros_like(D)], tau=1e-10)
+    with pytest.raises(FsimError):
+        bt.fock(FSIM_DFLOAT)
+    bt.close()
