@@ -152,8 +152,9 @@ __host__ __device__ constexpr bool dfloat_kernel(int X, int Y) { return !(X == 5
 // Default kernel of a class pair in an FSIM_DFLOAT build (the autotuner times
 // both): double-float up to total angular momentum 4, where the Boys function
 // and the prologue weigh most (measured on (H2O)_8: 3-8x faster than FP64);
-// FP64 from 5, where the contraction's dependent double-float chains at 255
-// registers leave the FP32 pipe latency-bound and the two kernels run even.
+// FP64 from 5, where R and the chunk's W outgrow 255 registers at two per value
+// and live in L1-backed local memory, which the double-float kernel, at 15 FP32
+// instructions per multiply-add, cannot feed fast enough: the two run even.
 __host__ __device__ constexpr bool dfloat_default(int X, int Y) {
   return dfloat_kernel(X, Y) && pair_cls_la(X) + pair_cls_lb(X) + pair_cls_la(Y) + pair_cls_lb(Y) <= 4;
 }
