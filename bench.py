@@ -114,17 +114,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-KERNEL_SOURCES = ["eri_core.cuh", "eri_launch.cuh", "boys.cuh", "md_tables.cuh", "fsim_internal.h"]
+KERNEL_SOURCES = ["eri_core.cuh", "eri_launch.cuh", "boys.cuh", "md_tables.cuh", "fsim_internal.h", "dfloat.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
 
 
 def kernel_source_digest() -> str:
-    """sha256 over the sources that define the Fock-build kernels."""
+    """sha256 over the code of the sources that define the Fock-build kernels: line
+    comments, trailing blanks and empty lines removed, so that an edited comment
+    keeps a capture valid while any code change invalidates it."""
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2510_24968_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2510_24968_gb300", "csrc", f), encoding="utf-8") as fh:
+            for line in fh.read().splitlines():
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()
 
 
