@@ -245,6 +245,8 @@ typedef struct {
   int incremental;      /* build G(D_n) as G(D_{n-1}) + G(D_n - D_{n-1}) */
 } fsim_scf_opts;
 
+/* Defaults: 100 iterations, |dE| 1e-10, rms(dD) 1e-7, DIIS 8, core-H guess, the Fock
+ * defaults, final_fp64 2 (double-float resets), incremental builds. */
 void fsim_scf_opts_default(fsim_scf_opts* o);
 
 typedef struct {

@@ -223,7 +223,7 @@ void fsim_scf_opts_default(fsim_scf_opts* o) {
   o->guess = FSIM_GUESS_CORE;
   o->D0 = nullptr;
   fsim_fock_opts_default(&o->fock);
-  o->final_fp64 = 1;
+  o->final_fp64 = 2;  // resets as double-float builds: FP64-accurate, ~2x faster on GB300
   o->incremental = 1;
 }
 

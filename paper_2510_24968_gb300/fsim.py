@@ -308,7 +308,7 @@ class Basis:
         return g.reshape(N, N, N, N)
 
     def scf(self, nelec=None, precision=FSIM_FP64, tau=1e-10, max_iter=100, conv_dE=1e-10, conv_dD=1e-7,
-            diis_size=8, D0=None, final_fp64=True, incremental=True, stream=None, want_density=False):
+            diis_size=8, D0=None, final_fp64=2, incremental=True, stream=None, want_density=False):
         o = fsim_scf_opts_default()
         o.nelec = self.mol.nelec if nelec is None else nelec
         o.max_iter, o.conv_dE, o.conv_dD, o.diis_size = max_iter, conv_dE, conv_dD, diis_size
