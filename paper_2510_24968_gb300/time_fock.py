@@ -4,7 +4,8 @@
 
 Prints one JSON object: per precision the build time of each repetition
 (CUDA events on the launching stream), the screened unique quartet count,
-quartets/s and the per-class-pair kernel times of a separate timed build.
+quartets/s and the per-class-pair kernel times and quartet counts of a separate
+timed build.
 Every step runs in libfsim; this module only draws the seeded density and
 reads the results.  Also the fixed command line used for kernel profiles.
 """
@@ -74,6 +75,7 @@ def main(argv=None):
         ms, qs, nl = gb.last_class_times()
         out[name] = {"build_ms": ts, "quartets": q, "quartets_per_s": q / (min(ts) * 1e-3),
                      "class_ms": {f"{_NAMES[x]}|{_NAMES[y]}": round(v, 4) for (x, y), v in ms.items()},
+                     "class_quartets": {f"{_NAMES[x]}|{_NAMES[y]}": int(v) for (x, y), v in qs.items() if v},
                      "launches": nl}
         if a.scf:
             t0 = time.perf_counter()
