@@ -6,9 +6,10 @@ recursion, Hermite-to-Cartesian contraction and J/K digestion of every unique
 shell quartet that survives Schwarz screening) of the seeded (H2O)_8 cluster
 (152 Cartesian functions, tau = 1e-10) in mixed precision (FP32 integrals,
 FP64 J/K accumulation).  Basis, pair data, Schwarz bounds and quartet lists
-are built once before timing.  value = ERI quartets/s; the FP64 Fock build,
-Fock builds/s and the time to an RHF energy within 1e-8 Eh (mixed vs FP64)
-are reported beside it.
+are built once before timing.  value = ERI quartets/s; the FP64 and the
+double-float (FP64-accurate, FP32 pipe) Fock builds, Fock builds/s and the
+time to an RHF energy within 1e-8 Eh (FP64, double-float, mixed with
+double-float or FP64 resets) are reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
