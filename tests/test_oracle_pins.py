@@ -307,6 +307,20 @@ def test_eri_rotation_covariance():
     assert np.abs(pred - u1).max() < 1e-12
 
 
+def test_eri_translation_invariance():
+    # moving every centre by the same vector leaves every ERI of an s/p/d molecule unchanged
+    rng = np.random.default_rng(12)
+    m = random_mol(rng, natom=3, lmax=2, nprim=2)
+    shift = np.array([2.3, -1.1, 0.6])
+    m2 = make_mol([(z, tuple(x + shift)) for z, x in zip(m.Z, m.xyz)],
+                  [(s.atom, s.l, s.alpha, s.coef) for s in m.shells])
+    B, B2 = OracleBasis(m), OracleBasis(m2)
+    ns = m.nshell
+    for q in [(0, 1, 2, 3), (2, 2, 5, 5), (8, 5, 2, 7), (3, 4, 6, 8), (5, 8, 8, 2)]:
+        q = tuple(x % ns for x in q)
+        assert np.abs(B.eri_block(*q) - B2.eri_block(*q)).max() < 1e-12
+
+
 def test_eri_far_field():
     # separated s distributions: (ab|cd) -> S_ab S_cd / R
     a, b, c, d = 1.0, 1.3, 0.9, 1.1
