@@ -13,10 +13,26 @@ double-float or FP64 resets) are reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-With N > 1 (torchrun, one rank per GPU) the bra pairs are sharded over the
-ranks (fsim_fock_opts.shard) and J, K are summed with one NCCL all-reduce per
-build: the same total work on N GPUs (strong scaling).  --impl reference times
-the CPU oracle (tests-only code) on a bounded sample of the same workload.
+With N > 1 (one rank per GPU; started through torch.distributed.run, or by
+this script itself when --gpus N > 1 comes without a launcher) the bra pairs
+are sharded over the ranks (fsim_fock_opts.shard) and J, K are summed with one
+NCCL all-reduce per build: the same total work on N GPUs (strong scaling).
+--impl reference times the CPU oracle (tests-only code) on a bounded sample of
+the same workload.
+
+At N = 1 the line also carries the 60-heavy-atom organic cloud (1140
+functions, tau = 1e-11): mixed builds with the FP32 large-T Boys branch and
+with FP64 Boys above T = 30, and an FP64-accurate (double-float / FP64 kernel
+mix) build of one bra-pair shard, with quartets/s, Fock builds/s and the
+roofline of its mixed build.
+
+Roofline flop counts: "method" counts what Eq. twoe-final asks for per
+primitive quartet -- the R recursion and the Hermite-to-Cartesian sums over
+the non-zero E^{ab}_{tuv} only (t <= i_x + j_x etc.), the first of the two
+transforms per primitive quartet and the second amortised over the other
+side's primitive pairs, whichever order is cheaper -- plus 12 flops per
+integral of J/K digestion; "dense" is the Hermite-dense count (every t, u, v
+up to the pair's total angular momentum), reported only as an equivalent rate.
 """
 from __future__ import annotations
 
@@ -54,10 +70,12 @@ PAIR_L = [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (2, 2)]
 
 
 def flops_per_quartet(X, Y, nprim=NPRIM):
-    """Algorithmic flops of one contracted quartet of class pair (X|Y):
+    """Hermite-dense flops of one contracted quartet of class pair (X|Y):
     per primitive quartet 2 sum_n n_h(L-n) (R recursion) +
-    2 min(A H1 H2 + A C H2, C H1 H2 + A C H1) (Hermite contraction), plus
-    12 A C per contracted quartet (J/K digestion, 6 FMA per integral)."""
+    2 min(A H1 H2 + A C H2, C H1 H2 + A C H1) (Hermite contraction with every
+    Hermite index of the pair), plus 12 A C per contracted quartet (J/K
+    digestion, 6 FMA per integral).  An equivalent rate only: the method never
+    touches the E^{ab}_{tuv} that vanish (t > i_x + j_x etc.)."""
     (la, lb), (lc, ld) = PAIR_L[X], PAIR_L[Y]
     L = la + lb + lc + ld
     A, Cc = ncart(la) * ncart(lb), ncart(lc) * ncart(ld)
@@ -65,6 +83,38 @@ def flops_per_quartet(X, Y, nprim=NPRIM):
     rec = 2 * sum(nherm(L - n) for n in range(L + 1))
     con = 2 * min(A * H1 * H2 + A * Cc * H2, Cc * H1 * H2 + A * Cc * H1)
     return nprim ** 4 * (rec + con) + 12 * A * Cc
+
+
+def cart_components(l):
+    return [(a, b, l - a - b) for a in range(l, -1, -1) for b in range(l - a, -1, -1)]
+
+
+def pair_nnz(la, lb):
+    """Non-zero E^{ab}_{tuv} over the Cartesian components of a pair class:
+    sum over (a, b) of prod_axis (i_axis + j_axis + 1)."""
+    n = 0
+    for ca in cart_components(la):
+        for cb in cart_components(lb):
+            n += (ca[0] + cb[0] + 1) * (ca[1] + cb[1] + 1) * (ca[2] + cb[2] + 1)
+    return n
+
+
+def method_flops_per_quartet(X, Y, nprim=NPRIM):
+    """Flops of one contracted quartet as Eq. twoe-final asks for them: per
+    primitive quartet the R recursion (2 sum_n n_h(L-n)) and the first transform
+    (2 H_other nnz_side), the second transform (2 nnz_other n_c(side)) once per
+    primitive pair of its side, cheaper order of the two; plus 12 flops per
+    integral of J/K digestion.  Boys evaluations are not counted."""
+    (la, lb), (lc, ld) = PAIR_L[X], PAIR_L[Y]
+    L = la + lb + lc + ld
+    A, Cc = ncart(la) * ncart(lb), ncart(lc) * ncart(ld)
+    H1, H2 = nherm(la + lb), nherm(lc + ld)
+    nzb, nzk = pair_nnz(la, lb), pair_nnz(lc, ld)
+    npp = nprim * nprim
+    rec = 2 * sum(nherm(L - n) for n in range(L + 1))
+    ket_first = 2 * H1 * nzk + 2 * nzb * Cc / npp   # W = E_cd R per primitive quartet, then E_ab W per bra pp
+    bra_first = 2 * H2 * nzb + 2 * nzk * A / npp
+    return npp * npp * (rec + min(ket_first, bra_first)) + 12 * A * Cc
 
 
 class ClockSampler:
@@ -206,27 +256,40 @@ def screened_quartets(mol, tau: float) -> int:
     return int(np.maximum(cut - np.arange(q.size), 0).sum())
 
 
+def bench_config(tau: float, world: int) -> dict:
+    """The workload both arms measure (identical dict on both lines)."""
+    return {"workload": WORKLOAD_DESC, "nbf": 152, "schwarz_tau": tau,
+            "step": "one Fock build J,K <- D over the screened unique shell quartets",
+            "l2": "GPU arm: 256 MiB device write before every timed step; CPU arm: no flush",
+            "parallelism": f"bra-pair shards x{world}" if world > 1 else "1 device"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
     from fsim_synth import workload
     mol = workload(WORKLOAD)
-    vals, desc = [], ""
-    per_step = 8.0
+    vals, secs, desc = [], [], ""
+    # each step is a bounded sample of the same build, sized so that the whole
+    # --steps/--warmup run stays within about 100 s of oracle time
+    per_step = max(1.0, min(8.0, 100.0 / (args.warmup + args.steps)))
     for it in range(args.warmup + args.steps):
         v, nq, dt, stride = cpu_sample(mol, per_step, args.tau)
         if it >= args.warmup:
             vals.append(v)
-        desc = f"bra pairs ij with ij % {stride} == 0 ({nq} unique quartets, {dt:.1f} s per step)"
+            secs.append(dt)
+        desc = f"oracle J/K over bra pairs ij with ij % {stride} == 0 ({nq} unique quartets per step)"
     v = statistics.mean(vals)
     cores = os.cpu_count()
     nq_full = screened_quartets(mol, args.tau)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": nq_full / v * 1e3,
-            "ms_per_step_note": f"one full build ({nq_full} quartets) at the sampled rate", "higher_is_better": True,
-            "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC, "precision": "FP64 oracle (plain C, OpenMP)"},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(secs) * 1e3,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": bench_config(args.tau, world),
+            "precision": "FP64 oracle (plain C, OpenMP over bra pairs)",
+            "full_build_ms_extrapolated": nq_full / v * 1e3,
+            "full_build_note": f"one full build ({nq_full} quartets) at the sampled rate (extrapolated)",
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -240,6 +303,81 @@ def time_to_energy(res, e_ref, tol=1e-8):
         if all(ok[i:]):
             return float(T[i])
     return None
+
+
+CLOUD_TAU = 1e-11
+CLOUD_SHARDS = 16
+
+
+def cloud60_section(args, gb_dev, sptr, flush):
+    """The 60-heavy-atom organic cloud (1140 functions, tau 1e-11): mixed builds
+    (FP32 large-T Boys branch; FP64 Boys above T = 30) and an FP64-accurate build
+    of one bra-pair shard (round-robin over the cost-sorted bra list), each timed
+    with per-class CUDA events (class pairs serialised on the stream)."""
+    import numpy as np
+    import torch
+
+    from fsim_synth import workload
+    from paper_2510_24968_gb300 import FSIM_DFLOAT, FSIM_MIXED, Basis
+    names = ["ss", "ps", "pp", "ds", "dp", "dd"]
+    mol = workload("cloud60")
+    t0 = time.perf_counter()
+    gb = Basis(mol)
+    gb.schwarz()
+    N = gb.nbf
+    Dn = np.random.default_rng(1).standard_normal((N, N)) * 0.02
+    D = torch.from_numpy(Dn + Dn.T).to(gb_dev)
+    J, K = torch.zeros_like(D), torch.zeros_like(D)
+    setup_s = time.perf_counter() - t0
+
+    def one(prec, b64=0.0, shard=0, nshards=1, timing=True):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(torch.cuda.current_stream())
+        gb.fock_build(D, J, K, tau=CLOUD_TAU, precision=prec, stream=sptr, boys_fp64_T=b64, shard=shard,
+                      nshards=nshards, timing=timing)
+        e1.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        t, q, _ = gb.last_class_times()
+        return e0.elapsed_time(e1), t, q
+
+    # first build: the plan is made on the host before the launches, the per-class
+    # events time only the GPU work of each class pair (serialised)
+    _, t_mx, q = one(FSIM_MIXED)
+    ms_mx, _, _ = one(FSIM_MIXED, timing=False)   # concurrent class-pair launches, as in the headline
+    _, t_b64, _ = one(FSIM_MIXED, b64=30.0)
+    ms_mx_ser, ms_b64 = sum(t_mx.values()), sum(t_b64.values())
+    nq = sum(q.values())
+    fl = sum(q[k] * method_flops_per_quartet(*k) for k in q)
+    dom = max(t_mx, key=t_mx.get)
+    dom_fl = q[dom] * method_flops_per_quartet(*dom)
+    _, t_df, q_df = one(FSIM_DFLOAT, shard=0, nshards=CLOUD_SHARDS)
+    ms_df = sum(t_df.values())
+    nq_df = sum(q_df.values())
+    return {
+        "workload": "organic cloud, 60 heavy atoms (C/N/O 70/15/15) on a jittered 2.8-bohr lattice, "
+                    f"4s3p1d per heavy atom, H-capped; {N} Cartesian functions, tau {CLOUD_TAU:g}",
+        "nbf": N, "unique_quartets": nq, "setup_s": setup_s,
+        "mixed_fp32_boys": {"ms": ms_mx, "eri_quartets_per_s": nq / (ms_mx * 1e-3), "fock_builds_per_s": 1e3 / ms_mx,
+                            "ms_serialised": ms_mx_ser},
+        "mixed_fp64_boys_T30": {"ms_serialised": ms_b64, "eri_quartets_per_s_serialised": nq / (ms_b64 * 1e-3),
+                                "fock_builds_per_s_serialised": 1e3 / ms_b64,
+                                "vs_fp32_boys_serialised": ms_b64 / ms_mx_ser},
+        "fp64_accurate_shard": {"precision": "double-float kernels up to L = 4, FP64 kernels above",
+                                "shard": f"0 of {CLOUD_SHARDS} (bra pairs i % {CLOUD_SHARDS} == 0)",
+                                "ms": ms_df, "unique_quartets": nq_df,
+                                "eri_quartets_per_s": nq_df / (ms_df * 1e-3),
+                                "full_build_ms_extrapolated": ms_df * nq / max(nq_df, 1)},
+        "build_roofline": {"flops": "method count", "achieved_tflops": fl / (ms_mx * 1e-3) / 1e12,
+                           "frac_fp32": fl / (ms_mx * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                           "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+        "dominant_kernel": {"class": f"{names[dom[0]]}|{names[dom[1]]}", "ms": t_mx[dom], "quartets": q[dom],
+                            "achieved_tflops": dom_fl / (t_mx[dom] * 1e-3) / 1e12,
+                            "frac_fp32": dom_fl / (t_mx[dom] * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                            "share_of_build": t_mx[dom] / sum(t_mx.values())},
+        "class_ms": {f"{names[k[0]]}|{names[k[1]]}": round(v, 3) for k, v in t_mx.items()},
+    }
 
 
 def run_ours(args):
@@ -332,10 +470,14 @@ def run_ours(args):
     tot = {k: sum(v) for k, v in cls_mixed.items()}
     dom = max(tot, key=tot.get)
     avg_ms = tot[dom] / len(cls_mixed[dom])
-    fl = qcls[dom] * flops_per_quartet(*dom)
+    fl = qcls[dom] * method_flops_per_quartet(*dom)
     achieved = fl / (avg_ms * 1e-3) / 1e12
+    dense_dom = qcls[dom] * flops_per_quartet(*dom) / (avg_ms * 1e-3) / 1e12
     names = ["ss", "ps", "pp", "ds", "dp", "dd"]
-    all_fl = sum(qcls[k] * flops_per_quartet(*k) for k in qcls)
+    all_fl = sum(qcls[k] * method_flops_per_quartet(*k) for k in qcls)
+    all_fl_dense = sum(qcls[k] * flops_per_quartet(*k) for k in qcls)
+    cloud = cloud60_section(args, gb_dev=dev, sptr=sptr, flush=flush) if rank == 0 and world == 1 \
+        and not args.no_cloud60 else None
 
     # end to end through the C-ABI with pinned host buffers (copies inside the timed region)
     Dh = torch.empty((N, N), dtype=torch.float64, pin_memory=True)
@@ -391,10 +533,9 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True, "scaling": "strong",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "nbf": N, "unique_quartets_per_build": q_mixed,
-                   "precision": "mixed: FP32 Boys/R/contraction, FP64 J/K accumulation",
-                   "step": "one Fock build J,K <- D", "l2": "256 MiB write before every timed step",
-                   "parallelism": f"bra-pair shards x{world}" if world > 1 else "1 GPU"},
+        "config": bench_config(args.tau, world),
+        "precision": "mixed: FP32 Boys/R/contraction, FP64 J/K accumulation",
+        "unique_quartets_per_build": q_mixed,
         "fock_builds_per_s": {"mixed": 1e3 / ms_mixed, "fp64": 1e3 / ms_fp64, "dfloat": 1e3 / ms_df},
         "eri_quartets_per_s": {"mixed": value, "fp64": q_fp64 / (ms_fp64 * 1e-3), "dfloat": q_df / (ms_df * 1e-3)},
         "class_ms_fp64_dfloat": {f"{names[k[0]]}|{names[k[1]]}": [round(sum(cls_fp64[k]) / len(cls_fp64[k]), 3),
@@ -405,13 +546,21 @@ def run_ours(args):
                      "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS,
                      "traffic": recorded_traffic(f"{names[dom[0]]}|{names[dom[1]]}"),
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                     "flops": "method count (E non-zeros only), per launch: quartets x "
+                              f"{method_flops_per_quartet(*dom):.0f}",
+                     "dense_equivalent_tflops": dense_dom,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (no measured FP32 peak)",
                      "share_of_build": tot[dom] / sum(tot.values()),
                      "timing": "per-launch CUDA events; class pairs serialised on the launching stream"},
-        "build_roofline": {"achieved": all_fl / (ms_mixed * 1e-3) / 1e12, "unit": "TFLOP/s",
+        "build_roofline": {"flops": "method count, all class pairs", "unit": "TFLOP/s",
+                           "achieved": all_fl / (ms_mixed * 1e-3) / 1e12,
                            "frac_fp32": all_fl / (ms_mixed * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
                            "fp64_achieved": all_fl / (ms_fp64 * 1e-3) / 1e12,
-                           "frac_fp64": all_fl / (ms_fp64 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS},
+                           "frac_fp64": all_fl / (ms_fp64 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                           "fp64_peak_source": "nominal 1.25 TFLOP/s FP64 (non-tensor)",
+                           "dense_equivalent_tflops": {"mixed": all_fl_dense / (ms_mixed * 1e-3) / 1e12,
+                                                       "fp64": all_fl_dense / (ms_fp64 * 1e-3) / 1e12}},
+        "cloud60": cloud,
         "class_ms": {f"{names[k[0]]}|{names[k[1]]}": round(tot[k] / len(cls_mixed[k]), 4) for k in tot},
         "autotune": {f"{names[k[0]]}|{names[k[1]]}": v[0] for k, v in tuned.items()},
         "autotune_fp64_dfloat": {f"{names[k[0]]}|{names[k[1]]}": [tuned_64[FSIM_FP64].get(k, (0,))[0],
@@ -438,13 +587,37 @@ def main():
     ap.add_argument("--no-scf", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-cloud60", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.gpus < 1:
+        sys.exit("bench.py: --gpus must be >= 1")
+    if "WORLD_SIZE" in os.environ:
+        if int(os.environ["WORLD_SIZE"]) != args.gpus:
+            sys.exit(f"bench.py: --gpus {args.gpus} but WORLD_SIZE={os.environ['WORLD_SIZE']}")
+    elif args.gpus > 1:
+        sys.exit(self_launch(args.gpus))
     if args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
+
+
+def self_launch(n: int) -> int:
+    """--gpus N > 1 without a launcher: start N ranks on this node through
+    torch.distributed.run (rendezvous on 127.0.0.1) and return their exit code."""
+    import socket
+    import torch
+    if torch.cuda.is_available() and torch.cuda.device_count() < n:
+        print(f"bench.py: --gpus {n} but only {torch.cuda.device_count()} visible GPU(s)", file=sys.stderr)
+        return 2
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        port = so.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
 
 
 if __name__ == "__main__":

@@ -164,13 +164,19 @@ int fsim_fock_build(fsim_basis* b, const double* D, double* J, double* K, const 
  * device array of 5 MiB that every GPU loading the library keeps until exit,
  * so the call allocates nothing.  Limits and rules:
  *  - nbf <= 512, else FSIM_EINVAL; D, J, K device pointers (ptr_mode
- *    FSIM_PTR_DEVICE); opts->timing must be 0;
+ *    FSIM_PTR_DEVICE); opts->timing must be 0; precision FSIM_FP64 or
+ *    FSIM_MIXED only (FSIM_DFLOAT: FSIM_EINVAL, it needs per-basis
+ *    double-float copies that are allocated); Cartesian bases only;
  *  - the basis must already hold its Schwarz bounds and the screening plan for
  *    these options: call fsim_fock_build once with the same opts during
  *    set-up (else FSIM_EINVAL, nothing launched);
- *  - the first call on a device looks up the array's device address (with the
- *    basis' device current); make that first call before any stream capture;
- *  - all calls share the array; calls whose GPU work overlaps race on it.
+ *  - that set-up build also looks up the array's device address on its device
+ *    (loading the module that holds the array), so later calls load nothing;
+ *    a first call on a device without that set-up does the look-up itself
+ *    (with the basis' device current): make it before any stream capture;
+ *  - all calls share the array; calls whose GPU work overlaps race on it;
+ *  - afterwards fsim_last_quartet_count reports this build; per-class times
+ *    (fsim_last_class_times) are not recorded (-1).
  */
 int fsim_fock_build_noalloc(fsim_basis* b, const double* D, double* J, double* K, const fsim_fock_opts* opts);
 

@@ -567,7 +567,9 @@ void orc_jk_shard(const void *vB, const double *D, double *J, double *K, double 
  * over ALL ordered shell pairs (c, d); with tau > 0 a quartet is skipped when
  * its Schwarz product is below tau (Q passed in, nshell x nshell), the same
  * rule as the unique-quartet loop since Q_ab Q_cd is permutation invariant.
- * Jb, Kb: na x nb row-major.  Used to check sampled blocks of large cases.
+ * A ket pair (c, d) whose density block D_cd is entirely zero adds nothing to
+ * either sum and is skipped.  Jb, Kb: na x nb row-major.  Used to check
+ * sampled blocks of large cases.
  */
 void orc_jk_block(const void *vB, const double *D, int sa, int sb, double *Jb, double *Kb,
                   double tau, const double *Q) {
@@ -585,6 +587,11 @@ void orc_jk_block(const void *vB, const double *D, int sa, int sb, double *Jb, d
             int nc = orc_ncart(B->l[sc]);
             for (int sd = 0; sd < ns; ++sd) {
                 int nd = orc_ncart(B->l[sd]);
+                int dz = 1;
+                for (int ic = 0; ic < nc && dz; ++ic)
+                    for (int id = 0; id < nd; ++id)
+                        if (D[(size_t)(B->ao[sc] + ic) * N + B->ao[sd] + id] != 0.0) { dz = 0; break; }
+                if (dz) continue;
                 if (!(tau > 0.0) || Q[sa * ns + sb] * Q[sc * ns + sd] >= tau) {
                     orc_eri_shell_quartet(vB, sa, sb, sc, sd, blk); /* (ab|cd) */
                     for (int ia = 0; ia < na; ++ia)

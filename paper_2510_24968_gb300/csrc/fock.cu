@@ -229,7 +229,12 @@ __global__ void symmetrize_kernel(const double* __restrict__ Ja, const double* _
 
 int ensure_scratch(fsim_basis* b) {
   const size_t n2 = (size_t)b->nbf * b->nbf;
-  if (!b->d_Jacc) FSIM_TRY(dev_alloc(&b->d_Jacc, n2));
+  if (!b->d_Jacc) {
+    // set-up of this basis on its device: also make the non-allocating entry
+    // point's fixed scratch resident here, so that its calls load nothing
+    FSIM_TRY(noalloc_scratch_prepare());
+    FSIM_TRY(dev_alloc(&b->d_Jacc, n2));
+  }
   if (!b->d_Kacc) FSIM_TRY(dev_alloc(&b->d_Kacc, n2));
   if (!b->d_D32) FSIM_TRY(dev_alloc(&b->d_D32, n2));
   return FSIM_OK;
@@ -653,6 +658,7 @@ static int launch_all_into(fsim_basis* b, FockPlan* plan, const Real* Dr, float 
                            double* Kacc, cudaStream_t s) {
   for (int X = kNumPairCls - 1; X >= 0; --X)
     for (int Y = X; Y >= 0; --Y) {
+      if (plan->cp[X][Y].nitems > 0) ++b->last_launches;
       const cudaError_t e = launch_cp<Real>(b, X, Y, plan->cp[X][Y], Dr, Jacc, Kacc, boys64_T, s);
       if (e != cudaSuccess) {
         set_error("J/K kernel (%d|%d): %s", X, Y, cudaGetErrorString(e));
@@ -694,12 +700,23 @@ int fock_build_into(fsim_basis* b, const double* dD, double* dJ, double* dK, con
   cudaStream_t s = (cudaStream_t)o.stream;
   const int N = b->nbf;
   const size_t n2 = (size_t)N * N;
+  // what fsim_last_quartet_count / fsim_last_class_times report for this build
+  b->last_timed = false;
+  b->last_stream = s;
+  b->last_launches = 0;
+  for (int X = 0; X < kNumPairCls; ++X)
+    for (int Y = 0; Y < kNumPairCls; ++Y) {
+      const int ci = X * kNumPairCls + Y;
+      b->last_class_run[ci] = Y <= X && plan->cp[X][Y].nitems > 0;
+      b->last_class_q[ci] = Y <= X ? plan->cp[X][Y].nquartets : 0;
+    }
   FSIM_CK(cudaMemsetAsync(Jacc, 0, n2 * sizeof(double), s));
   FSIM_CK(cudaMemsetAsync(Kacc, 0, n2 * sizeof(double), s));
   const float b64 = o.boys_fp64_T > 0.0 ? (float)o.boys_fp64_T : INFINITY;
   if (o.precision == FSIM_MIXED) {
     to_float_kernel<<<256, 256, 0, s>>>(dD, D32, n2);
     FSIM_CK(cudaGetLastError());
+    ++b->last_launches;
     FSIM_TRY(launch_all_into<float>(b, plan, D32, b64, Jacc, Kacc, s));
   } else {
     FSIM_TRY(launch_all_into<double>(b, plan, dD, b64, Jacc, Kacc, s));
@@ -707,6 +724,8 @@ int fock_build_into(fsim_basis* b, const double* dD, double* dJ, double* dK, con
   dim3 grid((N + 127) / 128, N);
   symmetrize_kernel<<<grid, 128, 0, s>>>(Jacc, Kacc, dJ, dK, N);
   FSIM_CK(cudaGetLastError());
+  ++b->last_launches;
+  b->last_quartets = plan->nquartets;
   return FSIM_OK;
 }
 

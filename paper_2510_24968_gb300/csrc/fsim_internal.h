@@ -278,6 +278,10 @@ int ensure_dfloat(fsim_basis* b);
 // out[i] = nearest dfloat of in[i]
 void launch_split(const double* in, dfloat* out, size_t n, cudaStream_t s);
 int ensure_scratch(fsim_basis* b);
+// Looks up, once per device (the current one), the device address of the fixed
+// scratch array of fsim_fock_build_noalloc; loading that array's module is the
+// only device memory this takes (noalloc.cu).
+int noalloc_scratch_prepare();
 int ensure_schwarz(fsim_basis* b);
 int device_sm_count();
 int build_pair_data(fsim_basis* b, int cls, const std::vector<int4>& order);

@@ -14,9 +14,14 @@
 //   * the array is shared by every call on a device and keeps the previous
 //     call's contents; the accumulators are cleared at the start of each call;
 //     calls whose GPU work overlaps (e.g. on two streams at once) race on it;
-//   * host code cannot use the array's name as a device address: on the first
-//     call on a device, with that device current, cudaGetSymbolAddress fetches
-//     the address once; make that first call before any stream capture.
+//   * host code cannot use the array's name as a device address: set-up
+//     fetches it with cudaGetSymbolAddress once per device, with that device
+//     current.  The first allocating build of a basis does this
+//     (noalloc_scratch_prepare, called when the basis allocates its own
+//     scratch), so the module that holds the array is loaded then and a later
+//     non-allocating call loads nothing; a first call on a device that never
+//     ran that set-up looks the address up itself, which may load the 5 MiB
+//     array, so it belongs in set-up too, before any stream capture.
 #include <mutex>
 
 #include "fsim_internal.h"
@@ -66,6 +71,11 @@ int scratch_address(void** out) {
 }
 
 }  // namespace
+
+int fsim::noalloc_scratch_prepare() {
+  void* p = nullptr;
+  return scratch_address(&p);
+}
 
 extern "C" int fsim_fock_build_noalloc(fsim_basis* b, const double* D, double* J, double* K,
                                        const fsim_fock_opts* opts) {

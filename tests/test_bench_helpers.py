@@ -46,3 +46,31 @@ def test_kernel_digest_ignores_comments_but_not_code(tmp_path, monkeypatch):
     assert bench.kernel_source_digest() == d0
     f.write_text(text.replace("constexpr int kJKThreads = 128;", "constexpr int kJKThreads = 256;"))
     assert bench.kernel_source_digest() != d0
+
+
+def test_pair_nnz_counts_the_non_vanishing_hermite_coefficients():
+    # E^{ij}_t vanishes outside 0 <= t <= i + j (Sec. 2.1.3); for random exponents and
+    # centres every coefficient inside that range is non-zero, so counting the oracle's
+    # non-zero coefficients per component pair must give the closed product form
+    from oracle import hermite_E
+    for la, lb, ref in ((0, 0, 1), (1, 0, 6), (1, 1, 33), (2, 2, 336)):
+        n = 0
+        for ca in bench.cart_components(la):
+            for cb in bench.cart_components(lb):
+                cnt = 1
+                for ax, X in enumerate((0.37, -0.52, 0.61)):
+                    cnt *= sum(1 for t in range(la + lb + 1)
+                               if abs(hermite_E(ca[ax], cb[ax], t, X, 0.8, 1.3)) > 1e-300)
+                n += cnt
+        assert n == ref == bench.pair_nnz(la, lb)
+
+
+def test_method_flops_hand_counts():
+    # (ss|ss): per primitive quartet R 2, ket transform 2*1*1, bra transform 2*1*1 / 9
+    assert bench.method_flops_per_quartet(0, 0) == 81 * (2 + 2 + 2 / 9) + 12
+    # (dd|dd): R 990, ket transform 2 * 35 * 336, bra transform 2 * 336 * 36 / 9
+    assert bench.method_flops_per_quartet(5, 5) == 81 * (990 + 2 * 35 * 336 + 2 * 336 * 36 / 9) + 12 * 1296
+    # never above the Hermite-dense count
+    for X in range(6):
+        for Y in range(X + 1):
+            assert bench.method_flops_per_quartet(X, Y) <= bench.flops_per_quartet(X, Y)
