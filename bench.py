@@ -352,6 +352,16 @@ def cloud60_section(args, gb_dev, sptr, flush):
     fl = sum(q[k] * method_flops_per_quartet(*k) for k in q)
     dom = max(t_mx, key=t_mx.get)
     dom_fl = q[dom] * method_flops_per_quartet(*dom)
+    J1 = torch.zeros_like(D)
+    gb.j_build(D, J1, tau=CLOUD_TAU, precision=FSIM_MIXED, stream=sptr)
+    flush.zero_()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(torch.cuda.current_stream())
+    gb.j_build(D, J1, tau=CLOUD_TAU, precision=FSIM_MIXED, stream=sptr)
+    e1.record(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    ms_j = e0.elapsed_time(e1)
     _, t_df, q_df = one(FSIM_DFLOAT, shard=0, nshards=CLOUD_SHARDS)
     ms_df = sum(t_df.values())
     nq_df = sum(q_df.values())
@@ -364,6 +374,7 @@ def cloud60_section(args, gb_dev, sptr, flush):
         "mixed_fp64_boys_T30": {"ms_serialised": ms_b64, "eri_quartets_per_s_serialised": nq / (ms_b64 * 1e-3),
                                 "fock_builds_per_s_serialised": 1e3 / ms_b64,
                                 "vs_fp32_boys_serialised": ms_b64 / ms_mx_ser},
+        "j_engine_mixed": {"ms": ms_j, "vs_fused_jk": ms_j / ms_mx, "ordered_quartets": gb.last_quartet_count()},
         "fp64_accurate_shard": {"precision": "double-float kernels up to L = 4, FP64 kernels above",
                                 "shard": f"0 of {CLOUD_SHARDS} (bra pairs i % {CLOUD_SHARDS} == 0)",
                                 "ms": ms_df, "unique_quartets": nq_df,
@@ -377,7 +388,35 @@ def cloud60_section(args, gb_dev, sptr, flush):
                             "frac_fp32": dom_fl / (t_mx[dom] * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
                             "share_of_build": t_mx[dom] / sum(t_mx.values())},
         "class_ms": {f"{names[k[0]]}|{names[k[1]]}": round(v, 3) for k, v in t_mx.items()},
+        "class_quartets": {f"{names[k[0]]}|{names[k[1]]}": int(v) for k, v in q.items() if v},
+        "class_frac_fp32": {f"{names[k[0]]}|{names[k[1]]}":
+                            round(q[k] * method_flops_per_quartet(*k) / (v * 1e-3) / 1e12 / FP32_PEAK_TFLOPS, 4)
+                            for k, v in t_mx.items() if v > 0},
+        "class_ms_fp64_boys_T30": {f"{names[k[0]]}|{names[k[1]]}": round(v, 3) for k, v in t_b64.items()},
     }
+
+
+def j_engine_times(gb, D, tau, sptr, flush, rank, world, reps=5):
+    """Coulomb-only builds (fsim_j_build, Hermite-space J-engine) against the
+    fused J/K build of the same screened quartets: CUDA events per build."""
+    import torch
+
+    from paper_2510_24968_gb300 import FSIM_FP64, FSIM_MIXED
+    out = {}
+    Jo = torch.zeros_like(D)
+    for name, prec in (("mixed", FSIM_MIXED), ("fp64", FSIM_FP64)):
+        gb.j_build(D, Jo, tau=tau, precision=prec, stream=sptr, shard=rank, nshards=world)  # plan
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(torch.cuda.current_stream())
+            gb.j_build(D, Jo, tau=tau, precision=prec, stream=sptr, shard=rank, nshards=world)
+            e1.record(torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        out[name] = {"ms": statistics.median(ts), "ordered_quartets": gb.last_quartet_count()}
+    return out
 
 
 def run_ours(args):
@@ -465,6 +504,7 @@ def run_ours(args):
     clk = clocks.stop()
     ms_fp64, q_fp64, cls_fp64, _, _ = timed(FSIM_FP64, max(2, min(args.steps, 3)), 1)
     ms_df, q_df, cls_df, _, _ = timed(FSIM_DFLOAT, max(2, min(args.steps, 3)), 1)
+    jeng = j_engine_times(gb, D, args.tau, sptr, flush, rank, world) if not args.no_jengine else None
 
     # roofline of the dominant kernel (largest time share of the mixed build)
     tot = {k: sum(v) for k, v in cls_mixed.items()}
@@ -561,6 +601,9 @@ def run_ours(args):
                            "dense_equivalent_tflops": {"mixed": all_fl_dense / (ms_mixed * 1e-3) / 1e12,
                                                        "fp64": all_fl_dense / (ms_fp64 * 1e-3) / 1e12}},
         "cloud60": cloud,
+        "j_engine": None if jeng is None else dict(jeng, **{
+            "note": "J alone by the Hermite-space J-engine (both orders of every screened unique quartet)",
+            "mixed_vs_fused_jk": jeng["mixed"]["ms"] / ms_mixed, "fp64_vs_fused_jk": jeng["fp64"]["ms"] / ms_fp64}),
         "class_ms": {f"{names[k[0]]}|{names[k[1]]}": round(tot[k] / len(cls_mixed[k]), 4) for k in tot},
         "autotune": {f"{names[k[0]]}|{names[k[1]]}": v[0] for k, v in tuned.items()},
         "autotune_fp64_dfloat": {f"{names[k[0]]}|{names[k[1]]}": [tuned_64[FSIM_FP64].get(k, (0,))[0],
@@ -588,6 +631,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-cloud60", action="store_true")
+    ap.add_argument("--no-jengine", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

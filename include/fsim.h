@@ -53,6 +53,8 @@ extern "C" {
 
 #define FSIM_GUESS_CORE 0     /* diagonalise H_core in the orthogonal basis (Sec. 3.2, step 1) */
 #define FSIM_GUESS_DENSITY 1  /* caller-supplied density fsim_scf_opts.D0 (checked; core-H fallback) */
+#define FSIM_GUESS_LEARNED 2  /* density predicted by the network in fsim_scf_opts.guess_model (checked;
+                                 core-H fallback) */
 
 typedef struct fsim_basis fsim_basis; /* opaque, owned by the library */
 
@@ -130,7 +132,9 @@ int fsim_schwarz(fsim_basis* b, double* Q);
 typedef struct {
   double schwarz_tau;  /* skip unique quartets with Q_ab Q_cd < tau; 0 = no screening */
   int precision;       /* FSIM_FP64, FSIM_MIXED or FSIM_DFLOAT */
-  double boys_fp64_T;  /* mixed path: Boys in FP64 for T >= this; 0 = never; values in (0, 30) are rejected */
+  double boys_fp64_T;  /* mixed path: Boys to FP64-level accuracy (double-float arithmetic on the FP32
+                          pipe, relative error <= 1e-13) for T >= this; 0 = never; values in (0, 30)
+                          are rejected */
   int ptr_mode;        /* FSIM_PTR_HOST or FSIM_PTR_DEVICE for D, J, K */
   void* stream;        /* cudaStream_t; NULL = legacy default stream */
   int shard;           /* this shard's index in [0, nshards): bra pairs i with i % nshards == shard */
@@ -179,6 +183,24 @@ int fsim_fock_build(fsim_basis* b, const double* D, double* J, double* K, const 
  *    (fsim_last_class_times) are not recorded (-1).
  */
 int fsim_fock_build_noalloc(fsim_basis* b, const double* D, double* J, double* K, const fsim_fock_opts* opts);
+
+/*
+ * Coulomb matrix alone, J_mu,nu = sum_{la,si} D_la,si (mu nu|la si) (Sec. 2.2
+ * Eq. fock), built in Hermite space without Cartesian quartets (Sec. 2.5: the
+ * ket's Hermite coefficients are contracted with the density first, so each
+ * primitive quartet costs the Hermite Coulomb recursion and
+ * n_h(L_bra) x n_h(L_ket) multiply-adds).  Same screening rule as
+ * fsim_fock_build (Q_ab Q_cd >= tau), evaluated over both orders of every
+ * screened unique quartet; fsim_last_quartet_count then reports that ordered
+ * count.  D, J: nbf*nbf row-major FP64, host or device per opts->ptr_mode (J
+ * overwritten).  opts: schwarz_tau, precision FSIM_FP64 or FSIM_MIXED (FP32
+ * integrals, FP64 accumulation), boys_fp64_T, ptr_mode, stream, shard/nshards
+ * (bra pairs i with i % nshards == shard; the caller sums J over shards);
+ * timing must be 0.  Cartesian bases only.  Errors: FSIM_EINVAL (null
+ * pointers, bad options, FSIM_DFLOAT, spherical basis), FSIM_ECUDA,
+ * FSIM_ENOMEM.
+ */
+int fsim_j_build(fsim_basis* b, const double* D, double* J, const fsim_fock_opts* opts);
 
 /*
  * Autotuner for the Fock-build launches of this basis and these options
@@ -249,6 +271,8 @@ typedef struct {
                            0 never, 1 FSIM_FP64 builds, 2 FSIM_DFLOAT builds (fsim_scf_batched:
                            any non-zero value means FSIM_FP64 builds) */
   int incremental;      /* build G(D_n) as G(D_{n-1}) + G(D_n - D_{n-1}) */
+  const char* guess_model; /* FSIM_GUESS_LEARNED: weights file written by fsim_mlp_save (its input and
+                              output widths must match fsim_guess_layout) */
 } fsim_scf_opts;
 
 /* Defaults: 100 iterations, |dE| 1e-10, rms(dD) 1e-7, DIIS 8, core-H guess, the Fock
@@ -269,6 +293,8 @@ typedef struct {
   long long quartets;   /* unique quartets evaluated over all Fock builds */
   int fp64_builds;      /* FP64-accurate Fock builds (FSIM_FP64 or FSIM_DFLOAT) */
   int mixed_builds;     /* Fock builds done in mixed precision */
+  double guess_s;       /* wall time of the initial density (prediction and check for a learned or
+                           supplied guess, core-H diagonalisation otherwise), inside the set-up */
 } fsim_scf_result;
 
 /*
@@ -346,6 +372,13 @@ int fsim_mlp_create(int nin, int width, int nout, const float* init_params, fsim
 void fsim_mlp_destroy(fsim_mlp* net);
 long long fsim_mlp_nparams(const fsim_mlp* net);
 int fsim_mlp_params(fsim_mlp* net, float* host_out, const float* host_in);
+/* Weights file of a network (the input of FSIM_GUESS_LEARNED): the 8 bytes
+ * "FSIMMLP1", int32 nin, width, nout (little-endian), then the
+ * fsim_mlp_nparams() FP32 master parameters in fsim_mlp_create's layout.
+ * fsim_mlp_load creates a new network from such a file (caller destroys it).
+ * Errors: FSIM_EINVAL (null pointers, unreadable or malformed file), FSIM_ECUDA. */
+int fsim_mlp_save(fsim_mlp* net, const char* path);
+int fsim_mlp_load(const char* path, fsim_mlp** out);
 int fsim_mlp_forward(fsim_mlp* net, const float* x, float* y, int batch, int bf16, void* stream);
 int fsim_mlp_grad(fsim_mlp* net, const float* x, const float* t, const float* mask, int batch, int bf16, float* loss,
                   float* grad_host, void* stream);

@@ -532,6 +532,18 @@ void fsim_basis_destroy(fsim_basis* b) {
       }
     delete p;
   }
+  for (auto* p : b->jplans) {
+    for (auto& row : p->cp)
+      for (auto& cp : row) {
+        dev_free(cp.d_prefix);
+        dev_free(cp.d_count);
+      }
+    delete p;
+  }
+  for (int X = 0; X < kNumPairCls; ++X) {
+    dev_free(b->d_rho32[X]);
+    dev_free(b->d_rho64[X]);
+  }
   dev_free(b->d_cen); dev_free(b->d_alpha); dev_free(b->d_coef); dev_free(b->d_nprim);
   dev_free(b->d_l); dev_free(b->d_ao); dev_free(b->d_axyz); dev_free(b->d_Z);
   dev_free(b->d_boys64); dev_free(b->d_boys32); dev_free(b->d_boysx); dev_free(b->d_Dx);

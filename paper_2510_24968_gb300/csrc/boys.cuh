@@ -12,9 +12,14 @@
 // FP64: h = 1/16, K = 8, table to T = 36 (truncation < 1e-16 relative).
 // FP32: h = 1/8, K = 5, table to T = 30; above T = 30 the asymptotic branch
 // runs in FP32 (F_0 = sqrt(pi/T)/2, e^{-T} kept in the upward recursion), or
-// in FP64 above a caller-chosen threshold `t64` (the policy of keeping Boys in
-// FP64 at large T; on GB300 FP64 issues at a small fraction of the FP32 rate,
-// so that policy is an option, not the default).
+// to FP64-level accuracy above a caller-chosen threshold `t64` (the policy of
+// keeping Boys in FP64 at large T).  That branch runs in double-float
+// arithmetic on the FP32 pipe: F_0 = (1/2) sqrt(pi) T^{-1/2} (erfc(sqrt 30) is
+// below 1e-14 of erf there) and the upward recursion in double-float, e^{-T}
+// from the FP32 exponential (e^{-T} <= 9.4e-14 enters F_n, n <= 8, T >= 30, at
+// most at ~1e-6 of its size, so FP32's relative error leaves ~1e-13).  The same
+// branch in native FP64 made the 60-atom cloud's mixed build 4x slower on
+// GB300, whose FP64 pipe issues 2 operations per clock and SM against 128 FP32.
 // Double-float (dfloat): the FP64 grid and K, everything in dfloat arithmetic
 // (see boys_dfloat); no FP64 operation.
 #pragma once
@@ -105,10 +110,19 @@ __device__ __forceinline__ void boys_fp32(float T, float (&F)[L + 1], const floa
       for (int n = 1; n <= L; ++n) F[n] = ((2 * n - 1) * F[n - 1] - e) * h;
     }
   } else {
-    double Fd[L + 1];
-    boys_asymptotic<L>((double)T, Fd);
-#pragma unroll
-    for (int n = 0; n <= L; ++n) F[n] = (float)Fd[n];
+    const dfloat rs = rsqrt_dfloat(dfloat(T, 0.0f));
+    dfloat Fd = dsplit(0.5 * kSqrtPi) * rs;
+    F[0] = Fd.hi;  // |lo| <= ulp(hi)/2: hi is the nearest float
+    if constexpr (L > 0) {
+      const dfloat e(expf(-T), 0.0f);
+      const dfloat rT = rs * rs;
+      const dfloat h(0.5f * rT.hi, 0.5f * rT.lo);
+      static_for<L>([&](auto I) {
+        constexpr int n = decltype(I)::value + 1;
+        Fd = (dfloat(2 * n - 1) * Fd - e) * h;
+        F[n] = Fd.hi;
+      });
+    }
   }
 }
 

@@ -245,6 +245,18 @@ __device__ __forceinline__ void quartet_chunk(Real* __restrict__ so, const BraAt
   }
 }
 
+// Barrier over the warps of chunk group g (0..3) of nthreads threads (a
+// multiple of 32): named barriers 1..4, id 0 being __syncthreads'.  The ids
+// are immediates so that a kernel reserves only the barriers it uses.
+__device__ __forceinline__ void group_barrier(int g, int nthreads) {
+  switch (g) {
+    case 0: asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory"); break;
+    case 1: asm volatile("bar.sync 2, %0;" ::"r"(nthreads) : "memory"); break;
+    case 2: asm volatile("bar.sync 3, %0;" ::"r"(nthreads) : "memory"); break;
+    default: asm volatile("bar.sync 4, %0;" ::"r"(nthreads) : "memory"); break;
+  }
+}
+
 // Binary search: largest i in [0, n) with prefix[i] <= item.
 __device__ __forceinline__ int find_bra(const int* __restrict__ prefix, int n, int item) {
   int lo = 0, hi = n - 1;
@@ -365,13 +377,13 @@ __global__ void __launch_bounds__(kJKThreads) jk_kernel(JKParams<Real> P) {
     const int4 bi = i >= 0 ? M.bra.idx[i] : make_int4(0, 0, 0, 0);
 #pragma unroll
     for (int a = 0; a < BC::NC; ++a) jb[a * kJKThreads] = Real(0);
-    if (valid) {
-      const int4 ki = M.ket.idx[j];
-      const int nppb = M.bra.npp[i];
-      const int nppk = M.ket.npp[j];
+    {
+      const int4 ki = valid ? M.ket.idx[j] : make_int4(0, 0, 0, 0);
+      const int nppb = valid ? M.bra.npp[i] : 0;
+      const int nppk = valid ? M.ket.npp[j] : 0;
       const Real deg = Real((bi.z == bi.w ? 1 : 2) * (ki.z == ki.w ? 1 : 2) * ((P.same && i == j) ? 1 : 2));
       const size_t bstride = (size_t)M.bra.ppmax * M.bra.n;
-      const Real* bpd = M.bra.pd + i;
+      const Real* bpd = M.bra.pd + (i >= 0 ? i : 0);
       const Real* Dbra = M.D + (size_t)bi.x * N + bi.y;
       auto bra = [&](int f, int pp) -> Real {
         if constexpr (kFlat) return ldg_r(bpd + (size_t)f * bstride + (size_t)pp * M.bra.n);
@@ -381,9 +393,29 @@ __global__ void __launch_bounds__(kJKThreads) jk_kernel(JKParams<Real> P) {
         if constexpr (kFlat) return ldg_r(Dbra + (size_t)(a / BC::NB) * N + a % BC::NB);
         else return sDab[a];
       };
+      // Every thread of a chunk group runs the same chunk iterations (valid
+      // quartet or not), so the group's named barrier below is always met.
 #pragma unroll 1
       for (int ch = cg; ch < KetChunks<KC, CS>::NCH; ch += ncg) {
-        quartet_chunk<Real, LA, LB, LC, LD, CS>(so, bra, nppb, bs, ps, M.ket, j, nppk, sBoys, BK, P.boys64_T, ch);
+        if (valid)
+          quartet_chunk<Real, LA, LB, LC, LD, CS>(so, bra, nppb, bs, ps, M.ket, j, nppk, sBoys, BK, P.boys64_T, ch);
+        if (ps > 1) {
+          // the ps threads of a quartet hold partial blocks over their bra
+          // primitive pairs: sum them into the first thread's slots (each
+          // element by one thread), which alone digests the chunk, so the
+          // J/K atomics are issued once per quartet instead of ps times
+          group_barrier(cg, gsz);
+          if (valid) {
+            Real* base = sOut + (threadIdx.x - bs);
+            for (int x = bs; x < BC::NC * CS; x += ps) {
+              Real acc = base[x * kJKThreads];
+              for (int r = 1; r < ps; ++r) acc += base[x * kJKThreads + r];
+              base[x * kJKThreads] = acc;
+            }
+          }
+          group_barrier(cg, gsz);
+        }
+        if (!valid || bs != 0) continue;
         auto out = [&](int a, int cs) -> Real { return so[(a * CS + cs) * kJKThreads]; };
         // digestion (Eq. fock) of this chunk
 #pragma unroll

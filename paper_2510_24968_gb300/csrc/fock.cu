@@ -299,7 +299,7 @@ static double class_cost(int X, int Y) {
   return 2.0 * r + 2.0 * std::min(A * H1 * H2 + A * C * H2, C * H1 * H2 + A * C * H1) + 16.0;
 }
 
-static int ensure_aux_streams(fsim_basis* b) {
+int ensure_aux_streams(fsim_basis* b) {
   if (b->aux_ok) return FSIM_OK;
   for (int k = 0; k < fsim_basis::kAuxStreams; ++k) {
     FSIM_CK(cudaStreamCreateWithFlags(&b->aux[k], cudaStreamNonBlocking));

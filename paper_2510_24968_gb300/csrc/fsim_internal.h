@@ -180,6 +180,16 @@ struct ClassPairPlan {
   int* d_count = nullptr;   // [nbra]
 };
 
+// Screened work lists of a Coulomb-only (J-engine) build: every ordered
+// (bra class X, ket class Y), kets j of bra i with Q_i Q_j >= tau.
+struct JPlan {
+  double tau = -1.0;
+  int shard = 0, nshards = 1;
+  int precision = 0;
+  ClassPairPlan cp[kNumPairCls][kNumPairCls];
+  long long nquartets = 0;
+};
+
 struct FockPlan {
   double tau = -1.0;
   int shard = 0, nshards = 1;
@@ -237,6 +247,10 @@ struct fsim_basis {
   fsim::dfloat* d_boysx = nullptr;  // double-float copy of the FP64 table (first FSIM_DFLOAT use)
   bool dfloat_ready = false;
   std::vector<fsim::FockPlan*> plans;
+  std::vector<fsim::JPlan*> jplans;
+  // density-contracted ket Hermite vectors of a J-engine build, per pair class
+  float* d_rho32[fsim::kNumPairCls] = {};
+  double* d_rho64[fsim::kNumPairCls] = {};
   long long last_quartets = 0;
   // scratch
   double* d_Jacc = nullptr;
@@ -283,6 +297,9 @@ int ensure_scratch(fsim_basis* b);
 // only device memory this takes (noalloc.cu).
 int noalloc_scratch_prepare();
 int ensure_schwarz(fsim_basis* b);
+int ensure_aux_streams(fsim_basis* b);
+// input, hidden and output widths of a network handle (mlp.cu)
+void mlp_dims(const fsim_mlp* net, int* nin, int* width, int* nout);
 int device_sm_count();
 int build_pair_data(fsim_basis* b, int cls, const std::vector<int4>& order);
 int run_list(fsim_basis* b, int X, int Y, const std::vector<int2>& items, double* d_out, int precision,

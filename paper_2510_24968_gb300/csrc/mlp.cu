@@ -13,6 +13,7 @@
 #include <cstdint>
 
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -289,6 +290,12 @@ int backward(fsim_mlp* n, const float* x, const float* t, const float* mask, int
 }  // namespace
 }  // namespace fsim
 
+void fsim::mlp_dims(const fsim_mlp* n, int* nin, int* width, int* nout) {
+  *nin = n->nin;
+  *width = n->width;
+  *nout = n->nout;
+}
+
 using namespace fsim;
 
 extern "C" {
@@ -344,6 +351,57 @@ int fsim_mlp_params(fsim_mlp* n, float* host_out, const float* host_in) {
     FSIM_CK(cudaDeviceSynchronize());
   }
   return FSIM_OK;
+}
+
+int fsim_mlp_save(fsim_mlp* n, const char* path) {
+  if (!n || !path) {
+    set_error("fsim_mlp_save: null pointer");
+    return FSIM_EINVAL;
+  }
+  std::vector<float> p(n->np);
+  FSIM_CK(cudaMemcpy(p.data(), n->p, sizeof(float) * n->np, cudaMemcpyDeviceToHost));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) {
+    set_error("fsim_mlp_save: cannot open %s", path);
+    return FSIM_EINVAL;
+  }
+  const int32_t dims[3] = {n->nin, n->width, n->nout};
+  const bool ok = std::fwrite("FSIMMLP1", 1, 8, f) == 8 && std::fwrite(dims, sizeof(int32_t), 3, f) == 3 &&
+                  std::fwrite(p.data(), sizeof(float), n->np, f) == n->np;
+  if (std::fclose(f) != 0 || !ok) {
+    set_error("fsim_mlp_save: write to %s failed", path);
+    return FSIM_EINVAL;
+  }
+  return FSIM_OK;
+}
+
+int fsim_mlp_load(const char* path, fsim_mlp** out) {
+  if (!path || !out) {
+    set_error("fsim_mlp_load: null pointer");
+    return FSIM_EINVAL;
+  }
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) {
+    set_error("fsim_mlp_load: cannot open %s", path);
+    return FSIM_EINVAL;
+  }
+  char magic[8];
+  int32_t dims[3];
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "FSIMMLP1", 8) == 0 &&
+            std::fread(dims, sizeof(int32_t), 3, f) == 3 && dims[0] > 0 && dims[1] > 0 && dims[2] > 0 &&
+            dims[0] <= 4096 && dims[1] <= 4096 && dims[2] <= 4096;
+  std::vector<float> p;
+  if (ok) {
+    p.resize(offsets(dims[0], dims[1], dims[2]).n);
+    ok = std::fread(p.data(), sizeof(float), p.size(), f) == p.size() && std::fgetc(f) == EOF;
+  }
+  std::fclose(f);
+  if (!ok) {
+    set_error("fsim_mlp_load: %s is not a weights file of fsim_mlp_save", path);
+    return FSIM_EINVAL;
+  }
+  return fsim_mlp_create(dims[0], dims[1], dims[2], p.data(), out);
 }
 
 int fsim_mlp_forward(fsim_mlp* n, const float* x, float* y, int batch, int bf16, void* stream) {

@@ -235,7 +235,8 @@ int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res) {
   const fsim_scf_opts& o = *opts;
   const int N = b->nbf_ext();
   if (o.nelec <= 0 || (o.nelec & 1) || o.nelec / 2 > N || o.max_iter < 1 || o.diis_size < 0 ||
-      (o.guess == FSIM_GUESS_DENSITY && !o.D0) || (o.guess != FSIM_GUESS_CORE && o.guess != FSIM_GUESS_DENSITY) ||
+      (o.guess == FSIM_GUESS_DENSITY && !o.D0) || (o.guess == FSIM_GUESS_LEARNED && !o.guess_model) ||
+      (o.guess != FSIM_GUESS_CORE && o.guess != FSIM_GUESS_DENSITY && o.guess != FSIM_GUESS_LEARNED) ||
       o.final_fp64 < 0 || o.final_fp64 > 2) {
     set_error("fsim_scf: bad options (nelec %d must be even and <= 2 nbf, max_iter %d, final_fp64 %d in 0..2)",
               o.nelec, o.max_iter, o.final_fp64);
@@ -314,11 +315,43 @@ int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res) {
     return FSIM_OK;
   };
   res->guess_fallback = 0;
-  if (o.guess == FSIM_GUESS_DENSITY) {
-    // supplied guess (e.g. the learned one): symmetrise, rescale to Tr(DS) = N_e,
+  const double t_guess0 = elapsed();
+  if (o.guess == FSIM_GUESS_LEARNED) {
+    // learned guess: pair features, the network's forward pass (BF16 weights,
+    // FP32 accumulation) and the rotation/assembly of its local blocks into tmp
+    if (b->spherical) {
+      set_error("fsim_scf: the learned guess works on Cartesian bases only");
+      return FSIM_EINVAL;
+    }
+    int npair = 0, nfeat = 0, nout = 0;
+    FSIM_TRY(fsim_guess_layout(b, &npair, &nfeat, &nout));
+    fsim_mlp* net = nullptr;
+    FSIM_TRY(fsim_mlp_load(o.guess_model, &net));
+    struct NetGuard {
+      fsim_mlp* n;
+      ~NetGuard() { fsim_mlp_destroy(n); }
+    } guard{net};
+    int nin = 0, width = 0, nout_net = 0;
+    mlp_dims(net, &nin, &width, &nout_net);
+    if (nin != nfeat || nout_net != nout) {
+      set_error("fsim_scf: guess model %s does not map %d features to %d block values", o.guess_model, nfeat, nout);
+      return FSIM_EINVAL;
+    }
+    std::vector<float> feat((size_t)npair * nfeat);
+    FSIM_TRY(fsim_guess_features(b, feat.data()));
+    float *xf, *yf;
+    FSIM_TRY(mem.alloc(&xf, feat.size()));
+    FSIM_TRY(mem.alloc(&yf, (size_t)npair * nout));
+    FSIM_CK(cudaMemcpyAsync(xf, feat.data(), sizeof(float) * feat.size(), cudaMemcpyHostToDevice, c.s));
+    FSIM_TRY(fsim_mlp_forward(net, xf, yf, npair, 1, c.s));
+    FSIM_TRY(fsim_guess_assemble(b, yf, tmp, c.s));
+  } else if (o.guess == FSIM_GUESS_DENSITY) {
+    FSIM_CK(cudaMemcpyAsync(tmp, o.D0, sizeof(double) * n2, cudaMemcpyHostToDevice, c.s));
+  }
+  if (o.guess == FSIM_GUESS_DENSITY || o.guess == FSIM_GUESS_LEARNED) {
+    // supplied or learned guess in tmp: symmetrise, rescale to Tr(DS) = N_e,
     // and keep it only if |Tr(DS) - N_e| <= 0.5 before rescaling and
     // ||D S D - 2 D||_F / ||D||_F <= 0.2 after; otherwise fall back to core-H
-    FSIM_CK(cudaMemcpyAsync(tmp, o.D0, sizeof(double) * n2, cudaMemcpyHostToDevice, c.s));
     antisym_kernel<<<g2, 128, 0, c.s>>>(tmp, e, N);           // e = D0 - D0^T
     add_kernel<<<bl, th, 0, c.s>>>(tmp, e, -0.5, D, n2);       // D = (D0 + D0^T) / 2
     const double tr = host_dot(c, scratch, D, S, n2, 0, &rc);
@@ -343,6 +376,8 @@ int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res) {
   } else {
     FSIM_TRY(density_from(H, D));
   }
+  FSIM_CK(cudaStreamSynchronize(c.s));
+  res->guess_s = elapsed() - t_guess0;
   res->e_nuc = 0.0;
   FSIM_TRY(fsim_enuc(b, &res->e_nuc));
 

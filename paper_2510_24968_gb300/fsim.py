@@ -30,16 +30,18 @@ FSIM_PTR_HOST = 0
 FSIM_PTR_DEVICE = 1
 FSIM_GUESS_CORE = 0
 FSIM_GUESS_DENSITY = 1
+FSIM_GUESS_LEARNED = 2
 
 # every symbol declared in include/fsim.h
 EXPORTS = ["fsim_basis_create", "fsim_basis_create_ex", "fsim_basis_destroy", "fsim_basis_nbf",
            "fsim_basis_nbf_cart", "fsim_basis_nshell",
            "fsim_basis_pair_counts", "fsim_enuc", "fsim_onee", "fsim_schwarz", "fsim_fock_opts_default",
-           "fsim_fock_build", "fsim_fock_build_noalloc", "fsim_autotune", "fsim_set_launch", "fsim_last_quartet_count", "fsim_last_class_times", "fsim_eri_quartets", "fsim_eri_dump",
+           "fsim_fock_build", "fsim_fock_build_noalloc", "fsim_j_build", "fsim_autotune", "fsim_set_launch", "fsim_last_quartet_count", "fsim_last_class_times", "fsim_eri_quartets", "fsim_eri_dump",
            "fsim_scf_opts_default", "fsim_scf", "fsim_batch_create", "fsim_batch_fock", "fsim_batch_destroy",
            "fsim_scf_batched", "fsim_guess_layout", "fsim_guess_features", "fsim_guess_targets",
            "fsim_guess_assemble", "fsim_mlp_create", "fsim_mlp_destroy", "fsim_mlp_nparams", "fsim_mlp_params",
-           "fsim_mlp_forward", "fsim_mlp_grad", "fsim_mlp_train_step", "fsim_last_error"]
+           "fsim_mlp_save", "fsim_mlp_load", "fsim_mlp_forward", "fsim_mlp_grad", "fsim_mlp_train_step",
+           "fsim_last_error"]
 
 
 class FsimError(RuntimeError):
@@ -66,7 +68,8 @@ class fsim_fock_opts(C.Structure):
 class fsim_scf_opts(C.Structure):
     _fields_ = [("nelec", C.c_int), ("max_iter", C.c_int), ("conv_dE", C.c_double), ("conv_dD", C.c_double),
                 ("diis_size", C.c_int), ("guess", C.c_int), ("D0", C.POINTER(C.c_double)),
-                ("fock", fsim_fock_opts), ("final_fp64", C.c_int), ("incremental", C.c_int)]
+                ("fock", fsim_fock_opts), ("final_fp64", C.c_int), ("incremental", C.c_int),
+                ("guess_model", C.c_char_p)]
 
 
 class fsim_scf_result(C.Structure):
@@ -74,7 +77,7 @@ class fsim_scf_result(C.Structure):
                 ("converged", C.c_int), ("guess_fallback", C.c_int), ("D_out", C.POINTER(C.c_double)),
                 ("e_hist", C.POINTER(C.c_double)), ("t_hist", C.POINTER(C.c_double)), ("time_s", C.c_double),
                 ("min_s_eig", C.c_double), ("quartets", C.c_longlong), ("fp64_builds", C.c_int),
-                ("mixed_builds", C.c_int)]
+                ("mixed_builds", C.c_int), ("guess_s", C.c_double)]
 
 
 _lib = None
@@ -106,6 +109,7 @@ def load():
     L.fsim_fock_opts_default.restype = None
     L.fsim_fock_build.argtypes = [vp, vp, vp, vp, C.POINTER(fsim_fock_opts)]
     L.fsim_fock_build_noalloc.argtypes = [vp, vp, vp, vp, C.POINTER(fsim_fock_opts)]
+    L.fsim_j_build.argtypes = [vp, vp, vp, C.POINTER(fsim_fock_opts)]
     L.fsim_autotune.argtypes = [vp, C.POINTER(fsim_fock_opts), ip, C.POINTER(C.c_float)]
     L.fsim_set_launch.argtypes = [vp, C.POINTER(fsim_fock_opts), ip]
     L.fsim_last_quartet_count.argtypes = [vp]
@@ -133,6 +137,8 @@ def load():
     L.fsim_mlp_nparams.argtypes = [vp]
     L.fsim_mlp_nparams.restype = C.c_longlong
     L.fsim_mlp_params.argtypes = [vp, fp, fp]
+    L.fsim_mlp_save.argtypes = [vp, C.c_char_p]
+    L.fsim_mlp_load.argtypes = [C.c_char_p, C.POINTER(vp)]
     L.fsim_mlp_forward.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp]
     L.fsim_mlp_grad.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int, fp, fp, vp]
     L.fsim_mlp_train_step.argtypes = [vp, vp, vp, vp, C.c_int, C.c_float, fp, vp]
@@ -254,6 +260,22 @@ class Basis:
         _check(load().fsim_fock_build(self.h, pD, pJ, pK, C.byref(o)))
         return J, K
 
+    def j_build(self, D, J=None, tau=1e-10, precision=FSIM_FP64, stream=None, shard=0, nshards=1,
+                boys_fp64_T=0.0):
+        """J alone for density D by the Hermite-space J-engine (numpy -> host mode; CUDA torch
+        tensors -> device mode)."""
+        if J is None:
+            J = np.zeros((self.nbf, self.nbf)) if isinstance(D, np.ndarray) else D.new_zeros(D.shape)
+        o = fsim_fock_opts_default()
+        o.schwarz_tau, o.precision, o.shard, o.nshards = tau, precision, shard, nshards
+        o.boys_fp64_T = boys_fp64_T
+        pD, mode = _ptr_of(D)
+        pJ, _ = _ptr_of(J)
+        o.ptr_mode = mode
+        o.stream = stream or 0
+        _check(load().fsim_j_build(self.h, pD, pJ, C.byref(o)))
+        return J
+
     def autotune(self, tau=1e-10, precision=FSIM_MIXED, stream=None, shard=0, nshards=1):
         """Tune the launch shape of every class pair; returns {(X, Y): (choice, ms)}."""
         o = fsim_fock_opts_default()
@@ -308,7 +330,8 @@ class Basis:
         return g.reshape(N, N, N, N)
 
     def scf(self, nelec=None, precision=FSIM_FP64, tau=1e-10, max_iter=100, conv_dE=1e-10, conv_dD=1e-7,
-            diis_size=8, D0=None, final_fp64=2, incremental=True, stream=None, want_density=False):
+            diis_size=8, D0=None, final_fp64=2, incremental=True, stream=None, want_density=False,
+            guess_model=None):
         o = fsim_scf_opts_default()
         o.nelec = self.mol.nelec if nelec is None else nelec
         o.max_iter, o.conv_dE, o.conv_dD, o.diis_size = max_iter, conv_dE, conv_dD, diis_size
@@ -320,6 +343,10 @@ class Basis:
             d0 = np.ascontiguousarray(D0, dtype=np.float64)
             keep.append(d0)
             o.guess, o.D0 = FSIM_GUESS_DENSITY, _dptr(d0)
+        elif guess_model is not None:
+            path = os.fsencode(guess_model)
+            keep.append(path)
+            o.guess, o.guess_model = FSIM_GUESS_LEARNED, path
         r = fsim_scf_result()
         eh = np.full(max_iter, np.nan)
         th = np.full(max_iter, np.nan)
@@ -334,7 +361,7 @@ class Basis:
                 "converged": bool(r.converged), "rc": rc, "time_s": r.time_s, "min_s_eig": r.min_s_eig,
                 "quartets": r.quartets, "fp64_builds": r.fp64_builds, "mixed_builds": r.mixed_builds,
                 "energies": eh[:n].copy(), "times": th[:n].copy(), "D": Dout,
-                "guess_fallback": bool(r.guess_fallback)}
+                "guess_fallback": bool(r.guess_fallback), "guess_s": r.guess_s}
 
 
 class Batch:

@@ -83,6 +83,11 @@ class GuessNet:
         except Exception:
             pass
 
+    def save(self, path):
+        """Weights file for fsim_scf's learned guess (FSIM_GUESS_LEARNED, guess_model)."""
+        import os
+        _check(load().fsim_mlp_save(self.h, os.fsencode(path)))
+
     def params(self) -> np.ndarray:
         out = np.zeros(self.np, dtype=np.float32)
         _check(load().fsim_mlp_params(self.h, _fp(out), None))

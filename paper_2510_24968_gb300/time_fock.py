@@ -36,6 +36,7 @@ def main(argv=None):
     ap.add_argument("--boys-fp64-T", type=float, default=0.0)
     ap.add_argument("--scf", action="store_true", help="also run the SCF to convergence")
     ap.add_argument("--spherical", action="store_true", help="real solid-harmonic basis")
+    ap.add_argument("--jengine", action="store_true", help="also time Coulomb-only J-engine builds")
     a = ap.parse_args(argv)
 
     mol = workload(a.workload)
@@ -77,6 +78,18 @@ def main(argv=None):
                      "class_ms": {f"{_NAMES[x]}|{_NAMES[y]}": round(v, 4) for (x, y), v in ms.items()},
                      "class_quartets": {f"{_NAMES[x]}|{_NAMES[y]}": int(v) for (x, y), v in qs.items() if v},
                      "launches": nl}
+        if a.jengine and prec != FSIM_DFLOAT:
+            gb.j_build(D, J, tau=a.tau, precision=prec, boys_fp64_T=a.boys_fp64_T)
+            tj = []
+            for _ in range(a.reps):
+                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s.record()
+                gb.j_build(D, J, tau=a.tau, precision=prec, boys_fp64_T=a.boys_fp64_T)
+                e.record()
+                torch.cuda.synchronize()
+                tj.append(s.elapsed_time(e))
+            out[name]["jengine_ms"] = tj
+            out[name]["jengine_ordered_quartets"] = gb.last_quartet_count()
         if a.scf:
             t0 = time.perf_counter()
             r = gb.scf(precision=prec, tau=a.tau)

@@ -98,19 +98,52 @@ def test_bad_guess_falls_back_to_core():
     assert abs(bad["e_total"] - core["e_total"]) < 1e-10
 
 
-def test_learned_guess_saves_iterations_small():
+def test_learned_guess_saves_iterations_small(tmp_path):
+    # the network's guess, supplied as D0 and run inside fsim_scf from its weights
+    # file (FSIM_GUESS_LEARNED): fewer iterations than core-H, the same energy
     from paper_2510_24968_gb300 import FSIM_MIXED, Basis
     from paper_2510_24968_gb300.guess import GuessNet, predict_density, train, training_data
     train_mols = [water_cluster(k, geom_seed=10**6 + i) for i, k in enumerate([2, 3, 4] * 20)]
     X, T, M, _ = training_data(train_mols)
     net = GuessNet(seed=3)
     train(net, X, T, M, steps=1500, batch=2048, lr0=1e-3)
+    path = tmp_path / "guess.fsimmlp"
+    net.save(path)
     gain = []
     for i in range(2):
         b = Basis(water_cluster(4, geom_seed=2 * 10**6 + i))
         core = b.scf(precision=FSIM_MIXED, tau=1e-10)
         learned = b.scf(precision=FSIM_MIXED, tau=1e-10, D0=predict_density(b, net))
+        inlib = b.scf(precision=FSIM_MIXED, tau=1e-10, guess_model=path)
         assert core["converged"] and learned["converged"] and not learned["guess_fallback"]
         assert abs(learned["e_total"] - core["e_total"]) < 1e-8
+        assert inlib["converged"] and not inlib["guess_fallback"] and inlib["guess_s"] > 0
+        assert abs(inlib["e_total"] - core["e_total"]) < 1e-8 and abs(inlib["iters"] - learned["iters"]) <= 1
         gain.append(core["iters"] - learned["iters"])
     assert sum(gain) > 0
+
+
+def test_weights_file_round_trip_and_rejections(tmp_path):
+    from paper_2510_24968_gb300 import FSIM_FP64, Basis, FsimError
+    from paper_2510_24968_gb300.fsim import load
+    from paper_2510_24968_gb300.guess import GuessNet
+    import ctypes as C
+    import os
+    net = GuessNet(width=40, seed=9)
+    path = tmp_path / "w.fsimmlp"
+    net.save(path)
+    h = C.c_void_p()
+    assert load().fsim_mlp_load(os.fsencode(path), C.byref(h)) == 0
+    back = GuessNet.__new__(GuessNet)
+    back.h, back.np = h, load().fsim_mlp_nparams(h)
+    assert np.array_equal(back.params(), net.params())
+    b = Basis(water_cluster(2, geom_seed=3))
+    # a network whose output width is not the block layout's
+    bad = GuessNet(nout=100, seed=1)
+    bad.save(tmp_path / "bad.fsimmlp")
+    with pytest.raises(FsimError):
+        b.scf(precision=FSIM_FP64, tau=1e-10, guess_model=tmp_path / "bad.fsimmlp")
+    # a file that is not a weights file
+    (tmp_path / "junk").write_bytes(b"FSIMMLP1" + b"\x00" * 7)
+    with pytest.raises(FsimError):
+        b.scf(precision=FSIM_FP64, tau=1e-10, guess_model=tmp_path / "junk")
