@@ -273,6 +273,10 @@ typedef struct {
   int incremental;      /* build G(D_n) as G(D_{n-1}) + G(D_n - D_{n-1}) */
   const char* guess_model; /* FSIM_GUESS_LEARNED: weights file written by fsim_mlp_save (its input and
                               output widths must match fsim_guess_layout) */
+  int dw_screen;        /* 1: density-weighted screening of the incremental builds (Sec. 5, direct SCF):
+                           G(dD) skips quartets with Q_ab Q_cd max|dD| < schwarz_tau (the threshold
+                           tau / max|dD|, rounded down to tau times a power of two, is the build's
+                           schwarz_tau); full builds keep schwarz_tau.  0 (default): off */
 } fsim_scf_opts;
 
 /* Defaults: 100 iterations, |dE| 1e-10, rms(dD) 1e-7, DIIS 8, core-H guess, the Fock
@@ -290,7 +294,7 @@ typedef struct {
                            loop (after the set-up) to the end of each iteration */
   double time_s;        /* wall time of the SCF loop */
   double min_s_eig;     /* smallest eigenvalue of S */
-  long long quartets;   /* unique quartets evaluated over all Fock builds */
+  long long quartets;   /* unique quartets evaluated over all Fock builds (after any density weighting) */
   int fp64_builds;      /* FP64-accurate Fock builds (FSIM_FP64 or FSIM_DFLOAT) */
   int mixed_builds;     /* Fock builds done in mixed precision */
   double guess_s;       /* wall time of the initial density (prediction and check for a learned or
@@ -378,6 +382,12 @@ int fsim_mlp_params(fsim_mlp* net, float* host_out, const float* host_in);
  * fsim_mlp_load creates a new network from such a file (caller destroys it).
  * Errors: FSIM_EINVAL (null pointers, unreadable or malformed file), FSIM_ECUDA. */
 int fsim_mlp_save(fsim_mlp* net, const char* path);
+/* One Adam step (the same update as fsim_mlp_train_step) from a gradient the
+ * caller supplies (host, fsim_mlp_nparams() floats): for data-parallel
+ * training, where each rank's fsim_mlp_grad of its share of a minibatch is
+ * combined over the ranks (weighted by each share's mask sum, since the loss
+ * is normalised per call) before every replica takes the same step. */
+int fsim_mlp_adam_step(fsim_mlp* net, const float* grad_host, float lr, void* stream);
 int fsim_mlp_load(const char* path, fsim_mlp** out);
 int fsim_mlp_forward(fsim_mlp* net, const float* x, float* y, int batch, int bf16, void* stream);
 int fsim_mlp_grad(fsim_mlp* net, const float* x, const float* t, const float* mask, int batch, int bf16, float* loss,

@@ -22,6 +22,39 @@ from fsim_synth import batched_set
 from .fsim import FSIM_FP64, FSIM_MIXED, Basis, scf_batched
 
 
+def partition(costs, world: int):
+    """Molecules over ranks, heaviest first onto the least loaded rank (the
+    molecules are independent: no exchange until the results are gathered)."""
+    load = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for i in sorted(range(len(costs)), key=lambda k: -costs[k]):
+        r = min(range(world), key=lambda q: load[q])
+        parts[r].append(i)
+        load[r] += costs[i]
+    return [sorted(p) for p in parts]
+
+
+def run_sharded(mols, solve, cost=lambda m: float(m.nbf) ** 4):
+    """Batched SCF over the ranks of the default process group: rank r solves
+    its share (solve(list of molecules) -> list of per-molecule results) and
+    the results are gathered back into the input order on every rank."""
+    import torch.distributed as dist
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    rank = dist.get_rank() if world > 1 else 0
+    parts = partition([cost(m) for m in mols], world)
+    mine = parts[rank]
+    res = solve([mols[i] for i in mine]) if mine else []
+    if world == 1:
+        return res
+    got = [None] * world
+    dist.all_gather_object(got, list(zip(mine, res)))
+    out = [None] * len(mols)
+    for chunk in got:
+        for i, r in chunk:
+            out[i] = r
+    return out
+
+
 def main(argv=None):
     import torch
 
@@ -37,6 +70,9 @@ def main(argv=None):
     a = ap.parse_args(argv)
 
     mols = batched_set(a.nmol, seed=a.seed, nmin=a.nmin, nmax=a.nmax)
+    import os
+    if int(os.environ.get("WORLD_SIZE", 1)) > 1:
+        return main_sharded(a, mols)
     t0 = time.perf_counter()
     bases = [Basis(m) for m in mols]
     for b in bases:
@@ -62,6 +98,39 @@ def main(argv=None):
         "in_call_setup_s": wall - float(th[-1]) if len(th) else None,
         "iteration_s": [float(x) for x in np.diff(np.concatenate([[0.0], th]))],
     }))
+
+
+def main_sharded(a, mols):
+    """One rank per GPU (torch.distributed.run): each rank runs the batched SCF
+    of its share of the molecules; rank 0 prints the gathered summary with the
+    slowest rank's wall time."""
+    import os
+
+    import torch
+    import torch.distributed as dist
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prec = FSIM_MIXED if a.precision == "mixed" else FSIM_FP64
+
+    def solve(ms):
+        bases = [Basis(m) for m in ms]
+        return scf_batched(bases, precision=prec, tau=a.tau, final_fp64=not a.no_fp64_reset, max_iter=a.max_iter)
+
+    dist.barrier()
+    t0 = time.perf_counter()
+    res = run_sharded(mols, lambda ms: [{k: v for k, v in r.items() if k in ("e_total", "iters", "converged", "time_s")}
+                                        for r in solve(ms)])
+    wall = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
+    dist.all_reduce(wall, op=dist.ReduceOp.MAX)
+    if dist.get_rank() == 0:
+        ok = [r for r in res if r["converged"]]
+        ts = sorted(r["time_s"] for r in ok) or [float("nan")]
+        print(json.dumps({"nmol": a.nmol, "ranks": dist.get_world_size(), "wall_s": wall.item(),
+                          "molecules_per_s": a.nmol / wall.item(), "converged": len(ok),
+                          "p50_s_converged": ts[len(ts) // 2],
+                          "p99_s_converged": ts[min(len(ts) - 1, int(0.99 * len(ts)))]}))
+    dist.destroy_process_group()
 
 
 if __name__ == "__main__":

@@ -434,6 +434,22 @@ int fsim_mlp_grad(fsim_mlp* n, const float* x, const float* t, const float* mask
   return FSIM_OK;
 }
 
+int fsim_mlp_adam_step(fsim_mlp* n, const float* grad_host, float lr, void* stream) {
+  if (!n || !grad_host || !(lr > 0.0f)) {
+    set_error("fsim_mlp_adam_step: bad arguments");
+    return FSIM_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  FSIM_CK(cudaMemcpyAsync(n->g, grad_host, sizeof(float) * n->np, cudaMemcpyHostToDevice, s));
+  ++n->step;
+  const float b1 = 0.9f, b2 = 0.999f;
+  adam_kernel<<<256, 256, 0, s>>>(n->p, n->g, n->m, n->v, n->pb, n->np, lr, b1, b2, 1e-8f,
+                                  1.0f - std::pow(b1, (float)n->step), 1.0f - std::pow(b2, (float)n->step));
+  FSIM_CK(cudaGetLastError());
+  FSIM_CK(cudaStreamSynchronize(s));
+  return FSIM_OK;
+}
+
 int fsim_mlp_train_step(fsim_mlp* n, const float* x, const float* t, const float* mask, int batch, float lr,
                         float* loss, void* stream) {
   if (!n || !x || !t || !mask || batch <= 0 || !(lr > 0.0f)) {

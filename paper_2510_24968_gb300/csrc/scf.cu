@@ -410,7 +410,23 @@ int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res) {
     fo.precision = want64 ? prec64 : FSIM_MIXED;
     if (o.incremental && have_G && !want64) {
       add_kernel<<<bl, th, 0, c.s>>>(D, Dn, -1.0, dD, n2);  // dD = D - D_prev (Dn holds D_prev)
+      if (o.dw_screen) {
+        // density-weighted screening: threshold tau / max|dD|, rounded down to
+        // tau 2^k so that the cached plans stay few
+        int imax = 0;
+        BLAS_CK(cublasIdamax(c.blas, (int)n2, dD, 1, &imax));
+        double dmax = 0.0;
+        FSIM_CK(cudaMemcpyAsync(&dmax, dD + (imax - 1), sizeof(double), cudaMemcpyDeviceToHost, c.s));
+        FSIM_CK(cudaStreamSynchronize(c.s));
+        dmax = std::fabs(dmax);
+        double t_eff = o.fock.schwarz_tau;
+        if (o.fock.schwarz_tau > 0.0 && dmax < 1.0)
+          t_eff = dmax > 0.0 ? std::ldexp(o.fock.schwarz_tau, std::min(60, (int)std::floor(-std::log2(dmax))))
+                             : std::ldexp(o.fock.schwarz_tau, 60);
+        fo.schwarz_tau = t_eff;
+      }
       FSIM_TRY(fock_build_ext_device(b, dD, J, K, fo));
+      fo.schwarz_tau = o.fock.schwarz_tau;
       add_kernel<<<bl, th, 0, c.s>>>(G, J, 1.0, G, n2);
       add_kernel<<<bl, th, 0, c.s>>>(G, K, -0.5, G, n2);
     } else {

@@ -40,7 +40,7 @@ EXPORTS = ["fsim_basis_create", "fsim_basis_create_ex", "fsim_basis_destroy", "f
            "fsim_scf_opts_default", "fsim_scf", "fsim_batch_create", "fsim_batch_fock", "fsim_batch_destroy",
            "fsim_scf_batched", "fsim_guess_layout", "fsim_guess_features", "fsim_guess_targets",
            "fsim_guess_assemble", "fsim_mlp_create", "fsim_mlp_destroy", "fsim_mlp_nparams", "fsim_mlp_params",
-           "fsim_mlp_save", "fsim_mlp_load", "fsim_mlp_forward", "fsim_mlp_grad", "fsim_mlp_train_step",
+           "fsim_mlp_save", "fsim_mlp_load", "fsim_mlp_adam_step", "fsim_mlp_forward", "fsim_mlp_grad", "fsim_mlp_train_step",
            "fsim_last_error"]
 
 
@@ -69,7 +69,7 @@ class fsim_scf_opts(C.Structure):
     _fields_ = [("nelec", C.c_int), ("max_iter", C.c_int), ("conv_dE", C.c_double), ("conv_dD", C.c_double),
                 ("diis_size", C.c_int), ("guess", C.c_int), ("D0", C.POINTER(C.c_double)),
                 ("fock", fsim_fock_opts), ("final_fp64", C.c_int), ("incremental", C.c_int),
-                ("guess_model", C.c_char_p)]
+                ("guess_model", C.c_char_p), ("dw_screen", C.c_int)]
 
 
 class fsim_scf_result(C.Structure):
@@ -138,6 +138,7 @@ def load():
     L.fsim_mlp_nparams.restype = C.c_longlong
     L.fsim_mlp_params.argtypes = [vp, fp, fp]
     L.fsim_mlp_save.argtypes = [vp, C.c_char_p]
+    L.fsim_mlp_adam_step.argtypes = [vp, C.POINTER(C.c_float), C.c_float, vp]
     L.fsim_mlp_load.argtypes = [C.c_char_p, C.POINTER(vp)]
     L.fsim_mlp_forward.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp]
     L.fsim_mlp_grad.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int, fp, fp, vp]
@@ -331,13 +332,14 @@ class Basis:
 
     def scf(self, nelec=None, precision=FSIM_FP64, tau=1e-10, max_iter=100, conv_dE=1e-10, conv_dD=1e-7,
             diis_size=8, D0=None, final_fp64=2, incremental=True, stream=None, want_density=False,
-            guess_model=None):
+            guess_model=None, dw_screen=False):
         o = fsim_scf_opts_default()
         o.nelec = self.mol.nelec if nelec is None else nelec
         o.max_iter, o.conv_dE, o.conv_dD, o.diis_size = max_iter, conv_dE, conv_dD, diis_size
         o.fock.schwarz_tau, o.fock.precision = tau, precision
         o.fock.stream = stream or 0
         o.final_fp64, o.incremental = int(final_fp64), int(incremental)
+        o.dw_screen = int(dw_screen)
         keep = []
         if D0 is not None:
             d0 = np.ascontiguousarray(D0, dtype=np.float64)

@@ -88,6 +88,11 @@ class GuessNet:
         import os
         _check(load().fsim_mlp_save(self.h, os.fsencode(path)))
 
+    def adam_step(self, grad: np.ndarray, lr: float, stream=0):
+        """One Adam step from a supplied gradient (host FP32, nparams values)."""
+        g = np.ascontiguousarray(grad, dtype=np.float32)
+        _check(load().fsim_mlp_adam_step(self.h, _fp(g), float(lr), C.c_void_p(stream)))
+
     def params(self) -> np.ndarray:
         out = np.zeros(self.np, dtype=np.float32)
         _check(load().fsim_mlp_params(self.h, _fp(out), None))
@@ -160,6 +165,58 @@ def train(net: GuessNet, X, T, M, steps=2000, batch=4096, lr0=1e-3, seed=11, log
         loss = net.train_step(xb.data_ptr(), tb.data_ptr(), mb.data_ptr(), batch, lr, want_loss=bool(want))
         if want:
             losses.append((s, loss))
+    return losses
+
+
+def combine_gradients(grad: np.ndarray, mask_sum: float) -> np.ndarray:
+    """Gradient of the whole minibatch from each rank's share of it.  The loss
+    is sum(mask (y - t)^2) / sum(mask) per call, so a share's gradient is
+    weighted by its mask sum: g = sum_r w_r g_r / sum_r w_r (one all-reduce of
+    the weighted gradient and the weight; the identity on one rank)."""
+    import torch
+    import torch.distributed as dist
+    buf = torch.from_numpy(np.concatenate([np.asarray(grad, dtype=np.float64) * mask_sum, [float(mask_sum)]]))
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        if dist.get_backend() == "nccl":
+            buf = buf.cuda()
+        dist.all_reduce(buf)
+        buf = buf.cpu()
+    return (buf[:-1] / buf[-1]).numpy().astype(np.float32)
+
+
+def train_data_parallel(net: GuessNet, X, T, M, steps=2000, batch=4096, lr0=1e-3, seed=11):
+    """Data-parallel training: every rank holds the same initial weights and its
+    own training shard; per step each rank draws a minibatch of batch/world rows
+    from its shard, the gradients are combined over the ranks
+    (combine_gradients) and every replica takes the same Adam step, so the
+    replicas stay equal.  Cosine learning-rate decay as in train()."""
+    import torch
+    import torch.distributed as dist
+
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    rank = dist.get_rank() if world > 1 else 0
+    dev = torch.device("cuda")
+    Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to(dev)
+    Td = torch.from_numpy(np.ascontiguousarray(T, dtype=np.float32)).to(dev)
+    Md = torch.from_numpy(np.ascontiguousarray(M, dtype=np.float32)).to(dev)
+    n = X.shape[0]
+    b = max(1, min(batch // world, n))
+    rng = SplitMix64(seed + 7919 * rank)
+    order = list(range(n))
+    pos = n
+    losses = []
+    for s in range(steps):
+        if pos + b > n:
+            rng.shuffle(order)
+            perm = torch.tensor(order, device=dev)
+            pos = 0
+        idx = perm[pos:pos + b]
+        pos += b
+        xb, tb, mb = Xd.index_select(0, idx), Td.index_select(0, idx), Md.index_select(0, idx)
+        loss, g = net.grad(xb.data_ptr(), tb.data_ptr(), mb.data_ptr(), b, bf16=True)
+        g = combine_gradients(g, float(mb.sum().item()))
+        net.adam_step(g, lr0 * 0.5 * (1 + math.cos(math.pi * s / steps)))
+        losses.append(loss)
     return losses
 
 

@@ -147,3 +147,55 @@ def test_weights_file_round_trip_and_rejections(tmp_path):
     (tmp_path / "junk").write_bytes(b"FSIMMLP1" + b"\x00" * 7)
     with pytest.raises(FsimError):
         b.scf(precision=FSIM_FP64, tau=1e-10, guess_model=tmp_path / "junk")
+
+
+@pytest.mark.parametrize("k,seed", [(2, 6), (4, 8)])
+def test_frames_features_blocks_match_oracle(k, seed):
+    # the library's pair features, local blocks and assembly against the numpy
+    # restatement (oracle/guess.py, whose rotation matrices come from least squares)
+    import ctypes as C
+    from oracle import OracleBasis
+    from oracle import guess as og
+    from paper_2510_24968_gb300 import Basis
+    from paper_2510_24968_gb300.guess import _check, features, load, targets
+    mol = water_cluster(k, geom_seed=seed)
+    b = Basis(mol)
+    assert np.abs(features(b) - og.features(mol)).max() < 1e-6
+    D = np.linalg.inv(OracleBasis(mol).onee("S"))
+    t, m = targets(b, D)
+    to, mo = og.targets(mol, D)
+    assert np.array_equal(m, mo.astype(np.float32))
+    assert np.abs(t - to).max() < 1e-6 * np.abs(to).max()
+    # assembly of the same float32 blocks
+    y = torch.from_numpy(t).cuda()
+    Dg = torch.zeros((b.nbf, b.nbf), dtype=torch.float64, device="cuda")
+    _check(load().fsim_guess_assemble(b.h, C.c_void_p(y.data_ptr()), C.c_void_p(Dg.data_ptr()), None))
+    Do = og.assemble(mol, t.astype(np.float64))
+    assert np.abs(Dg.cpu().numpy() - Do).max() < 1e-10 * max(1.0, np.abs(Do).max())
+
+
+def test_adam_step_from_combined_shares_equals_train_step():
+    # data-parallel update on one device: the gradients of two shares of a
+    # minibatch, combined with their mask sums, then fsim_mlp_adam_step, give the
+    # same parameters as fsim_mlp_train_step on the whole minibatch
+    from paper_2510_24968_gb300.guess import GuessNet
+    net, x, t, m = _net_and_data(width=64, b=512, seed=4)
+    twin = GuessNet(width=64, seed=5)
+    assert np.array_equal(twin.params(), net.params())
+    xd, td, md = (torch.from_numpy(a).cuda() for a in (x, t, m))
+    p0 = net.params().astype(np.float64)
+    for step in range(3):
+        net.train_step(xd.data_ptr(), td.data_ptr(), md.data_ptr(), 512, 1e-3)
+        num, den = 0.0, 0.0
+        for sl in (slice(0, 200), slice(200, 512)):
+            xs, ts, ms = xd[sl].contiguous(), td[sl].contiguous(), md[sl].contiguous()
+            _, g = twin.grad(xs.data_ptr(), ts.data_ptr(), ms.data_ptr(), ms.shape[0], bf16=True)
+            w = float(ms.sum().item())
+            num, den = num + g.astype(np.float64) * w, den + w
+        twin.adam_step((num / den).astype(np.float32), 1e-3)
+        torch.cuda.synchronize()
+    # Adam's first steps move each parameter by about lr times the sign of its
+    # gradient, so a component whose gradient rounds across zero can differ by
+    # 2 lr: compare the whole update in norm
+    da, db = net.params() - p0, twin.params() - p0
+    assert np.linalg.norm(da - db) < 1e-2 * np.linalg.norm(da)
