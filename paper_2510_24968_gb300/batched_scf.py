@@ -67,6 +67,7 @@ def main(argv=None):
     ap.add_argument("--max-iter", type=int, default=60)
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--no-fp64-reset", action="store_true", help="mixed without the final FP64 builds")
+    ap.add_argument("--dw-screen", action="store_true", help="density-weighted screening of the increments")
     a = ap.parse_args(argv)
 
     mols = batched_set(a.nmol, seed=a.seed, nmin=a.nmin, nmax=a.nmax)
@@ -81,7 +82,8 @@ def main(argv=None):
     setup = time.perf_counter() - t0
     prec = FSIM_MIXED if a.precision == "mixed" else FSIM_FP64
     t0 = time.perf_counter()
-    res = scf_batched(bases, precision=prec, tau=a.tau, final_fp64=not a.no_fp64_reset, max_iter=a.max_iter)
+    res = scf_batched(bases, precision=prec, tau=a.tau, final_fp64=not a.no_fp64_reset, max_iter=a.max_iter,
+                      dw_screen=a.dw_screen)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     ts = sorted(r["time_s"] for r in res)
@@ -90,7 +92,8 @@ def main(argv=None):
     print(json.dumps({
         "nmol": a.nmol, "heavy_atoms": [a.nmin, a.nmax], "nbf_range": [min(b.nbf for b in bases),
                                                                      max(b.nbf for b in bases)],
-        "precision": a.precision, "fp64_reset": not a.no_fp64_reset, "tau": a.tau, "setup_s": setup,
+        "precision": a.precision, "fp64_reset": not a.no_fp64_reset, "dw_screen": a.dw_screen, "tau": a.tau,
+        "setup_s": setup,
         "wall_s": wall, "molecules_per_s": a.nmol / wall, "converged": sum(r["converged"] for r in res),
         "p50_s": ts[len(ts) // 2], "p99_s": ts[min(len(ts) - 1, int(0.99 * len(ts)))],
         "mean_iters": float(np.mean([r["iters"] for r in res])),
@@ -115,7 +118,8 @@ def main_sharded(a, mols):
 
     def solve(ms):
         bases = [Basis(m) for m in ms]
-        return scf_batched(bases, precision=prec, tau=a.tau, final_fp64=not a.no_fp64_reset, max_iter=a.max_iter)
+        return scf_batched(bases, precision=prec, tau=a.tau, final_fp64=not a.no_fp64_reset, max_iter=a.max_iter,
+                           dw_screen=a.dw_screen)
 
     dist.barrier()
     t0 = time.perf_counter()

@@ -381,6 +381,8 @@ static int compute_schwarz(fsim_basis* b) {
       C.h_Q[j] = q[perm[j]];
     }
     FSIM_TRY(build_pair_data(b, X, order));
+    if (!C.d_Q) FSIM_TRY(dev_alloc(&C.d_Q, std::max(C.n, 1)));
+    if (C.n) FSIM_CK(cudaMemcpy(C.d_Q, C.h_Q.data(), sizeof(double) * C.n, cudaMemcpyHostToDevice));
   }
   FSIM_CK(cudaDeviceSynchronize());
   b->schwarz_done = true;
@@ -522,7 +524,7 @@ void fsim_basis_destroy(fsim_basis* b) {
   if (!b) return;
   for (auto& C : b->cls) {
     dev_free(C.idx); dev_free(C.npp); dev_free(C.pd64); dev_free(C.pd32); dev_free(C.pq64); dev_free(C.pq32);
-    dev_free(C.pdx); dev_free(C.pqx);
+    dev_free(C.pdx); dev_free(C.pqx); dev_free(C.d_Q);
   }
   for (auto* p : b->plans) {
     for (auto& row : p->cp)

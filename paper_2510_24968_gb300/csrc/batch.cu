@@ -80,6 +80,31 @@ __global__ void batch_prepare_kernel(const MolPtrs* __restrict__ m, const int* _
   }
 }
 
+// Density-weighted threshold per molecule of an incremental build:
+// tau / max|Din| (Din holds D_n - D_{n-1}); 0 for full builds (incr 0).
+__global__ void batch_dw_kernel(const MolPtrs* __restrict__ m, const int* __restrict__ incr, float* __restrict__ tau_mol,
+                                double tau) {
+  const int mol = blockIdx.x;
+  __shared__ double red[256];
+  double mx = 0.0;
+  if (incr[mol]) {
+    const MolPtrs M = m[mol];
+    const size_t n2 = (size_t)M.N * M.N;
+    for (size_t i = threadIdx.x; i < n2; i += blockDim.x) mx = fmax(mx, fabs(M.Din[i]));
+  }
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    if (incr[mol] && tau > 0.0) t = red[0] > 0.0 ? (float)fmin(tau / red[0], 1e30) : 1e30f;
+    tau_mol[mol] = t;
+  }
+}
+
 __global__ void batch_symmetrize_kernel(const MolPtrs* __restrict__ m, const int* __restrict__ active) {
   const int mol = blockIdx.y;
   if (!active[mol]) return;
@@ -110,6 +135,8 @@ struct fsim_batch {
   };
   CPB cp[2][fsim::kNumPairCls][fsim::kNumPairCls];
   int* d_active = nullptr;
+  float* d_tau = nullptr;  // per molecule density-weighted threshold (0: plain screening)
+  int* d_incr = nullptr;   // per molecule: 1 when its next build is an increment G(D_n - D_{n-1})
   fsim::MolPtrs* d_ptrs = nullptr;
   std::vector<fsim::MolPtrs> h_ptrs;
   int maxN = 0;
@@ -136,7 +163,7 @@ int build_tables(fsim_batch* bt, int prec) {
         if (cp.nitems == 0) continue;
         const Real* D = prec == 0 ? (const Real*)bt->h_ptrs[m].Din : (const Real*)bt->h_ptrs[m].D32;
         mols.push_back(JKMol<Real>{b->cls[X].view<Real>(), b->cls[Y].view<Real>(), cp.d_prefix, cp.d_count, b->nbf,
-                                   D, b->d_Jacc, b->d_Kacc});
+                                   D, b->d_Jacc, b->d_Kacc, b->cls[X].d_Q, b->cls[Y].d_Q});
         prefix.push_back(prefix.back() + cp.nitems);
         C.ids.push_back(m);
         C.bra_ppmax = std::max(C.bra_ppmax, b->cls[X].ppmax);
@@ -180,6 +207,7 @@ int launch_batch(fsim_batch* bt, int prec, cudaStream_t s, bool dry) {
         p.mols = (const JKMol<Real>*)C.d_mols;
         p.mol_prefix = C.d_prefix;
         p.active = bt->d_active;
+        p.tau_mol = bt->d_tau;
         p.mol_ids = C.d_ids;
         p.nmol = C.nin;
         p.nitems = dry ? 0 : C.nitems;
@@ -246,11 +274,13 @@ int fsim_batch_create(fsim_basis* const* bases, int nmol, const fsim_fock_opts* 
     bt->h_ptrs.push_back(MolPtrs{b->d_Jacc, b->d_Kacc, b->d_D32, D[m], J[m], K[m], b->nbf});
     bt->maxN = std::max(bt->maxN, b->nbf);
   }
-  if ((rc = dev_alloc(&bt->d_ptrs, nmol)) != FSIM_OK || (rc = dev_alloc(&bt->d_active, nmol)) != FSIM_OK)
+  if ((rc = dev_alloc(&bt->d_ptrs, nmol)) != FSIM_OK || (rc = dev_alloc(&bt->d_active, nmol)) != FSIM_OK ||
+      (rc = dev_alloc(&bt->d_tau, nmol)) != FSIM_OK || (rc = dev_alloc(&bt->d_incr, nmol)) != FSIM_OK)
     return fail(rc);
   std::vector<int> ones(nmol, 1);
   if (cudaMemcpy(bt->d_ptrs, bt->h_ptrs.data(), sizeof(MolPtrs) * nmol, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(bt->d_active, ones.data(), sizeof(int) * nmol, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaMemcpy(bt->d_active, ones.data(), sizeof(int) * nmol, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(bt->d_tau, 0, sizeof(float) * nmol) != cudaSuccess) {
     set_error("fsim_batch_create: upload failed");
     return fail(FSIM_ECUDA);
   }
@@ -272,6 +302,8 @@ void fsim_batch_destroy(fsim_batch* bt) {
       }
   }
   dev_free(bt->d_active);
+  dev_free(bt->d_tau);
+  dev_free(bt->d_incr);
   dev_free(bt->d_ptrs);
   delete bt;
 }
@@ -577,7 +609,7 @@ extern "C" int fsim_scf_batched(fsim_basis* const* bases, int nmol, const fsim_s
     FSIM_TRY(fsim_batch_create(bases, nmol, &fo, Din.data(), Jp.data(), Kp.data(), &bt));
   }
   const double t_loop0 = elapsed();
-  std::vector<int> act64(nmol), actmx(nmol);
+  std::vector<int> act64(nmol), actmx(nmol), incr_h(nmol, 0);
   int nconv = 0, it = 0;
   for (it = 1; it <= o.max_iter && nconv < nmol; ++it) {
     bool any64 = false, anymx = false;
@@ -593,6 +625,13 @@ extern "C" int fsim_scf_batched(fsim_basis* const* bases, int nmol, const fsim_s
         FSIM_CK(cudaMemcpyAsync(m.Din, m.D, sizeof(double) * m.n2, cudaMemcpyDeviceToDevice, s0));
       (m.want64 ? act64 : actmx)[i] = 1;
       (m.want64 ? any64 : anymx) = true;
+    }
+    if (o.dw_screen) {
+      // density-weighted thresholds of this iteration's increments (full builds: 0)
+      for (int i = 0; i < nmol; ++i) incr_h[i] = !mols[i].conv && mols[i].incr && !mols[i].want64;
+      FSIM_CK(cudaMemcpyAsync(bt->d_incr, incr_h.data(), sizeof(int) * nmol, cudaMemcpyHostToDevice, s0));
+      batch_dw_kernel<<<nmol, 256, 0, s0>>>(bt->d_ptrs, bt->d_incr, bt->d_tau, o.fock.schwarz_tau);
+      FSIM_CK(cudaGetLastError());
     }
     if (any64) FSIM_TRY(fsim_batch_fock(bt, FSIM_FP64, act64.data(), 1));
     if (anymx) FSIM_TRY(fsim_batch_fock(bt, FSIM_MIXED, actmx.data(), 1));

@@ -67,6 +67,8 @@ struct JKMol {
   const Real* __restrict__ D;           // density, N x N, in the working precision
   double* J;                            // accumulators (FP64), N x N
   double* K;
+  const double* __restrict__ bq = nullptr;  // Schwarz bounds of the bra / ket class's pairs (same order);
+  const double* __restrict__ kq = nullptr;  // read only when JKParams::tau_mol is set
 };
 
 template <typename Real>
@@ -84,6 +86,9 @@ struct JKParams {
   int bra_ppmax;                        // largest bra primitive-pair count (shared-memory size)
   const Real* __restrict__ boys;
   float boys64_T;                       // FP32 path: Boys in FP64 at T >= this (infinity = never)
+  // batched, optional: per molecule (indexed like active) a density-weighted
+  // threshold; a quartet with Q_ab Q_cd below it is skipped (0: none skipped)
+  const float* __restrict__ tau_mol = nullptr;
 };
 
 // Hermite Coulomb integrals R^0_{tuv} for t+u+v <= L, in place (Eq. R-recursion):
@@ -339,10 +344,12 @@ __global__ void __launch_bounds__(kJKThreads) jk_kernel(JKParams<Real> P) {
 
   for (int item = blockIdx.x; item < P.nitems; item += gridDim.x) {
     int litem = item;
+    int mol_id = 0;
     const JKMol<Real>* Mp = &P.one;
     if (P.nmol > 0) {
       const int m = find_bra(P.mol_prefix, P.nmol, item);
-      if (P.active && !__ldg(P.active + __ldg(P.mol_ids + m))) continue;  // uniform per CTA: a converged molecule
+      mol_id = __ldg(P.mol_ids + m);
+      if (P.active && !__ldg(P.active + mol_id)) continue;  // uniform per CTA: a converged molecule
       Mp = P.mols + m;
       litem = item - __ldg(P.mol_prefix + m);
     }
@@ -373,6 +380,12 @@ __global__ void __launch_bounds__(kJKThreads) jk_kernel(JKParams<Real> P) {
       __syncthreads();
       j = tile * tq + q;
       valid = q < tq && j < __ldg(M.ket_count + i);
+    }
+    if (P.tau_mol != nullptr && valid) {
+      // density-weighted screening of an incremental build: every term this
+      // quartet adds is bounded by Q_ab Q_cd max|dD|, compared here with tau / max|dD|
+      const float te = __ldg(P.tau_mol + mol_id);
+      if (te > 0.0f && (float)(__ldg(M.bq + i) * __ldg(M.kq + j)) < te) valid = false;
     }
     const int4 bi = i >= 0 ? M.bra.idx[i] : make_int4(0, 0, 0, 0);
 #pragma unroll

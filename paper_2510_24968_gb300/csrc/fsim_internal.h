@@ -66,6 +66,7 @@ struct DevClass {
   std::vector<int4> h_idx;  // host copy, same order
   std::vector<int> h_npp;
   std::vector<double> h_Q;  // Schwarz bound of each pair, same order
+  double* d_Q = nullptr;    // device copy of h_Q
   int nfield() const { return 4 + nnz; }
   template <typename Real>
   PairView<Real> view() const;

@@ -400,7 +400,7 @@ class Batch:
 
 
 def scf_batched(bases, precision=FSIM_MIXED, tau=1e-10, max_iter=100, conv_dE=1e-10, conv_dD=1e-7, diis_size=8,
-                final_fp64=True, incremental=True, stream=None):
+                final_fp64=True, incremental=True, stream=None, want_density=False, dw_screen=False):
     """Lockstep RHF of many molecules; returns a list of per-molecule dicts."""
     n = len(bases)
     o = fsim_scf_opts_default()
@@ -409,13 +409,19 @@ def scf_batched(bases, precision=FSIM_MIXED, tau=1e-10, max_iter=100, conv_dE=1e
     o.fock.schwarz_tau, o.fock.precision = tau, precision
     o.fock.stream = stream or 0
     o.final_fp64, o.incremental = int(final_fp64), int(incremental)
+    o.dw_screen = int(dw_screen)
     res = (fsim_scf_result * n)()
     hist = [np.full(max_iter, np.nan) for _ in range(n)]
     thist = [np.full(max_iter, np.nan) for _ in range(n)]
     for r, h, t in zip(res, hist, thist):
         r.e_hist, r.t_hist = _dptr(h), _dptr(t)
+    dens = [np.zeros((b.nbf, b.nbf)) for b in bases] if want_density else [None] * n
+    if want_density:
+        for r, d in zip(res, dens):
+            r.D_out = _dptr(d)
     hb = (C.c_void_p * n)(*[b.h.value for b in bases])
     rc = _check(load().fsim_scf_batched(hb, n, C.byref(o), res), allow=(FSIM_ENOCONV,))
     return [{"e_total": r.e_total, "iters": r.iters, "converged": bool(r.converged), "time_s": r.time_s,
              "fp64_builds": r.fp64_builds, "mixed_builds": r.mixed_builds, "rc": rc,
-             "energies": h[:r.iters].copy(), "times": t[:r.iters].copy()} for r, h, t in zip(res, hist, thist)]
+             "energies": h[:r.iters].copy(), "times": t[:r.iters].copy(), "D": d}
+            for r, h, t, d in zip(res, hist, thist, dens)]

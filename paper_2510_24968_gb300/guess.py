@@ -133,6 +133,29 @@ def training_data(mols, tau=1e-10):
     return np.concatenate(X), np.concatenate(T), np.concatenate(M), energies
 
 
+def training_data_batched(mols, tau=1e-10, chunk=256):
+    """training_data() through the library's batched lockstep SCF (mixed
+    precision, no FP64 reset: the targets are FP32 blocks), chunk molecules
+    per batch; molecules that do not converge are left out."""
+    from .fsim import scf_batched
+    X, T, M = [], [], []
+    energies = []
+    for c0 in range(0, len(mols), chunk):
+        bases = [Basis(m) for m in mols[c0:c0 + chunk]]
+        res = scf_batched(bases, precision=FSIM_MIXED, tau=tau, final_fp64=False, want_density=True)
+        for b, r in zip(bases, res):
+            if not r["converged"]:
+                continue
+            X.append(features(b))
+            t, m = targets(b, r["D"])
+            T.append(t)
+            M.append(m)
+            energies.append(r["e_total"])
+        for b in bases:
+            b.close()
+    return np.concatenate(X), np.concatenate(T), np.concatenate(M), energies
+
+
 def train(net: GuessNet, X, T, M, steps=2000, batch=4096, lr0=1e-3, seed=11, log_every=0):
     """Adam with cosine decay over `steps` minibatches (device-resident data)."""
     import torch

@@ -23,7 +23,7 @@ import numpy as np
 from fsim_synth import water_cluster
 
 from . import FSIM_MIXED, Basis
-from .guess import GuessNet, train, train_data_parallel, training_data
+from .guess import GuessNet, train, train_data_parallel, training_data, training_data_batched
 
 
 def time_to(res, e_ref, tol=1e-8):
@@ -42,6 +42,7 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--out", default=None)
     ap.add_argument("--save", default=None, help="write the trained weights (fsim_mlp_save) here")
+    ap.add_argument("--batched", action="store_true", help="converge the training clusters with fsim_scf_batched")
     a = ap.parse_args(argv)
     import os
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -57,7 +58,7 @@ def main(argv=None):
         rank = dist.get_rank()
     t0 = time.time()
     mols = [water_cluster(2 + i % 5, geom_seed=10**6 + i) for i in range(a.train) if i % world == rank]
-    X, T, M, _ = training_data(mols)
+    X, T, M, e_train = training_data_batched(mols) if a.batched else training_data(mols)
     t_data = time.time() - t0
     net = GuessNet(seed=3)
     t0 = time.time()
@@ -90,7 +91,7 @@ def main(argv=None):
                      "converged": core["converged"] and lrn["converged"]})
     ok = [r for r in rows if r["converged"]]
     summary = {
-        "train_clusters": a.train, "train_pairs": int(X.shape[0]), "steps": a.steps, "data_s": t_data,
+        "train_clusters": a.train, "train_converged": len(e_train), "train_pairs": int(X.shape[0]), "steps": a.steps, "data_s": t_data,
         "train_s": t_train, "loss_first_last": [losses[0][1], losses[-1][1]], "test_molecules": a.test,
         "converged_both": len(ok),
         "mean_iters_core": float(np.mean([r["core_iters"] for r in ok])),

@@ -92,6 +92,22 @@ def test_scf_batched_matches_single_and_oracle():
     assert abs(res64[0]["e_total"] - ro.e_total) < 1e-8
 
 
+def test_scf_batched_density_weighted_increments():
+    # the batched increments skip quartets below tau / max|dD| per molecule on the
+    # device; the energies stay those of the plain lockstep run, and densities
+    # come back with the right electron count
+    from paper_2510_24968_gb300 import FSIM_MIXED, Basis, scf_batched
+    mols = [water_cluster(2, geom_seed=7), water_cluster(3, geom_seed=9), water_cluster(4, geom_seed=5)]
+    bases = [Basis(m) for m in mols]
+    plain = scf_batched(bases, precision=FSIM_MIXED, tau=1e-10)
+    dw = scf_batched(bases, precision=FSIM_MIXED, tau=1e-10, dw_screen=True, want_density=True)
+    for b, m, rp, rd in zip(bases, mols, plain, dw):
+        assert rp["converged"] and rd["converged"]
+        assert abs(rd["e_total"] - rp["e_total"]) < 1e-8
+        S = b.onee("S")
+        assert abs(float(np.sum(rd["D"] * S)) - m.nelec) < 1e-6
+
+
 def test_scf_batched_uneven_set():
     # molecules of the batched workload generator (uneven heavy-atom counts): the
     # lockstep iteration must follow each molecule's own single-molecule SCF
