@@ -273,10 +273,14 @@ typedef struct {
   int incremental;      /* build G(D_n) as G(D_{n-1}) + G(D_n - D_{n-1}) */
   const char* guess_model; /* FSIM_GUESS_LEARNED: weights file written by fsim_mlp_save (its input and
                               output widths must match fsim_guess_layout) */
-  int dw_screen;        /* 1: density-weighted screening of the incremental builds (Sec. 5, direct SCF):
-                           G(dD) skips quartets with Q_ab Q_cd max|dD| < schwarz_tau (the threshold
-                           tau / max|dD|, rounded down to tau times a power of two, is the build's
-                           schwarz_tau); full builds keep schwarz_tau.  0 (default): off */
+  int dw_screen;        /* 1: density-weighted screening of the incremental builds (Sec. 5, direct SCF)
+                           of a FSIM_MIXED SCF while its mixed iteration settles: G(dD) skips quartets
+                           with Q_ab Q_cd max|dD| < schwarz_tau (fsim_scf: the threshold tau / max|dD|,
+                           rounded down to tau times a power of two, is the build's schwarz_tau;
+                           fsim_scf_batched: per molecule on the device).  The skipped terms add up in
+                           the incremental G, so the FP64-accurate resets and every build after the
+                           first one keep schwarz_tau (final_fp64 != 0 is needed for FP64-level
+                           energies).  0 (default): off */
 } fsim_scf_opts;
 
 /* Defaults: 100 iterations, |dE| 1e-10, rms(dD) 1e-7, DIIS 8, core-H guess, the Fock

@@ -37,14 +37,15 @@
 #endif
 
 #define ORC_PI 3.14159265358979323846264338327950288
-#define ORC_LMAX 2            /* s, p, d shells */
-#define ORC_NCMAX 6           /* Cartesian components of a d shell */
+#define ORC_LMAX 3            /* s, p, d, f shells */
+#define ORC_NCMAX 10          /* Cartesian components of an f shell */
 #define ORC_KMAX 8            /* primitives per shell */
 #define ORC_RMAX (4 * ORC_LMAX + 1)
 
 /* ------------------------------------------------------------------ */
 /* Cartesian components in lexicographic-descending order:            */
-/* p: x y z ; d: xx xy xz yy yz zz                                    */
+/* p: x y z ; d: xx xy xz yy yz zz ; f: xxx xxy xxz xyy xyz xzz yyy   */
+/* yyz yzz zzz                                                        */
 /* ------------------------------------------------------------------ */
 static int orc_ncart(int l) { return (l + 1) * (l + 2) / 2; }
 
@@ -116,9 +117,24 @@ typedef struct {
     double a, X, Y, Z;
     int S; /* stride = L + 1 */
     double F[4 * ORC_RMAX];
-    double val[ORC_RMAX * ORC_RMAX * ORC_RMAX * ORC_RMAX];
-    unsigned char have[ORC_RMAX * ORC_RMAX * ORC_RMAX * ORC_RMAX];
+    double *val;          /* S^4 memo entries */
+    unsigned char *have;
 } orc_rctx;
+
+static orc_rctx *orc_rctx_new(int L) {
+    orc_rctx *c = (orc_rctx *)malloc(sizeof(orc_rctx));
+    size_t n = (size_t)(L + 1) * (L + 1) * (L + 1) * (L + 1);
+    c->S = L + 1;
+    c->val = (double *)malloc(sizeof(double) * n);
+    c->have = (unsigned char *)malloc(n);
+    return c;
+}
+
+static void orc_rctx_free(orc_rctx *c) {
+    free(c->val);
+    free(c->have);
+    free(c);
+}
 
 static double orc_R(orc_rctx *c, int n, int t, int u, int v) {
     if (t < 0 || u < 0 || v < 0) return 0.0;
@@ -139,6 +155,7 @@ static double orc_R(orc_rctx *c, int n, int t, int u, int v) {
     return r;
 }
 
+/* c must come from orc_rctx_new(L) with the same L. */
 static void orc_rctx_init(orc_rctx *c, int L, double a, double X, double Y, double Z) {
     c->a = a; c->X = X; c->Y = Y; c->Z = Z;
     c->S = L + 1;
@@ -149,10 +166,10 @@ static void orc_rctx_init(orc_rctx *c, int L, double a, double X, double Y, doub
 
 /* Public single-value access (used by the pins). */
 double orc_hermite_R(int n, int t, int u, int v, double a, double X, double Y, double Z) {
-    orc_rctx *c = (orc_rctx *)malloc(sizeof(orc_rctx));
+    orc_rctx *c = orc_rctx_new(n + t + u + v);
     orc_rctx_init(c, n + t + u + v, a, X, Y, Z);
     double r = orc_R(c, n, t, u, v);
-    free(c);
+    orc_rctx_free(c);
     return r;
 }
 
@@ -271,7 +288,7 @@ static double orc_onee_prim(int which, const int *i3, const int *j3, double a, c
     for (int d = 0; d < 3; ++d) P[d] = (a * A[d] + b * B[d]) / p;
     int L = i3[0] + i3[1] + i3[2] + j3[0] + j3[1] + j3[2];
     double v = 0.0;
-    orc_rctx *c = (orc_rctx *)malloc(sizeof(orc_rctx));
+    orc_rctx *c = orc_rctx_new(L);
     for (int n = 0; n < Bs->natom; ++n) {
         const double *C = &Bs->axyz[3 * n];
         orc_rctx_init(c, L, p, P[0] - C[0], P[1] - C[1], P[2] - C[2]);
@@ -284,7 +301,7 @@ static double orc_onee_prim(int which, const int *i3, const int *j3, double a, c
                        * orc_hermite_E(i3[2], j3[2], w, X[2], a, b) * orc_R(c, 0, t, u, w);
         v += -Bs->Z[n] * (2.0 * ORC_PI / p) * s;
     }
-    free(c);
+    orc_rctx_free(c);
     return v;
 }
 
@@ -346,7 +363,7 @@ void orc_eri_shell_quartet(const void *vB, int sa, int sb, int sc, int sd, doubl
     for (int i = 0; i < nblk; ++i) out[i] = 0.0;
     int L = B->l[sa] + B->l[sb] + B->l[sc] + B->l[sd];
     const double *A = &B->cen[3 * sa], *Bc = &B->cen[3 * sb], *C = &B->cen[3 * sc], *D = &B->cen[3 * sd];
-    orc_rctx *rc = (orc_rctx *)malloc(sizeof(orc_rctx));
+    orc_rctx *rc = orc_rctx_new(L);
     for (int ka = 0; ka < B->nprim[sa]; ++ka)
     for (int kb = 0; kb < B->nprim[sb]; ++kb) {
         double a = B->alpha[sa * ORC_KMAX + ka], b = B->alpha[sb * ORC_KMAX + kb];
@@ -408,7 +425,7 @@ void orc_eri_shell_quartet(const void *vB, int sa, int sb, int sc, int sd, doubl
         }
     }
     }
-    free(rc);
+    orc_rctx_free(rc);
 }
 
 /* Full N^4 tensor g[mu][nu][la][si] (small N only). */

@@ -627,8 +627,11 @@ extern "C" int fsim_scf_batched(fsim_basis* const* bases, int nmol, const fsim_s
       (m.want64 ? any64 : anymx) = true;
     }
     if (o.dw_screen) {
-      // density-weighted thresholds of this iteration's increments (full builds: 0)
-      for (int i = 0; i < nmol; ++i) incr_h[i] = !mols[i].conv && mols[i].incr && !mols[i].want64;
+      // density-weighted thresholds of this iteration's increments while each
+      // molecule's mixed iteration settles (phase 0); 0 for full builds and from
+      // the FP64 reset on (the skipped terms add up in the incremental G)
+      for (int i = 0; i < nmol; ++i)
+        incr_h[i] = !mols[i].conv && mols[i].incr && !mols[i].want64 && mols[i].phase == 0;
       FSIM_CK(cudaMemcpyAsync(bt->d_incr, incr_h.data(), sizeof(int) * nmol, cudaMemcpyHostToDevice, s0));
       batch_dw_kernel<<<nmol, 256, 0, s0>>>(bt->d_ptrs, bt->d_incr, bt->d_tau, o.fock.schwarz_tau);
       FSIM_CK(cudaGetLastError());

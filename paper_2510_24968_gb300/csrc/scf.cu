@@ -410,9 +410,12 @@ int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res) {
     fo.precision = want64 ? prec64 : FSIM_MIXED;
     if (o.incremental && have_G && !want64) {
       add_kernel<<<bl, th, 0, c.s>>>(D, Dn, -1.0, dD, n2);  // dD = D - D_prev (Dn holds D_prev)
-      if (o.dw_screen) {
-        // density-weighted screening: threshold tau / max|dD|, rounded down to
-        // tau 2^k so that the cached plans stay few
+      if (o.dw_screen && phase == 0) {
+        // density-weighted screening while the mixed iteration settles:
+        // threshold tau / max|dD|, rounded down to tau 2^k so that the cached
+        // plans stay few.  The skipped terms are each below tau but add up in
+        // the incrementally built G, so from the FP64-accurate reset on every
+        // build keeps the plain threshold and the reset removes what was skipped
         int imax = 0;
         BLAS_CK(cublasIdamax(c.blas, (int)n2, dD, 1, &imax));
         double dmax = 0.0;

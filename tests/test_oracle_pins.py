@@ -174,7 +174,9 @@ def test_ssss_closed_form(a, b, c, d):
 
 CLASSES = [(1, 0, 0, 0), (1, 1, 0, 0), (1, 0, 1, 0), (1, 1, 1, 1), (2, 0, 0, 0), (2, 1, 0, 0),
            (2, 0, 2, 0), (2, 1, 1, 0), (2, 2, 0, 0), (2, 1, 2, 1), (2, 2, 1, 1), (2, 2, 2, 0), (2, 2, 2, 2),
-           (0, 2, 1, 2), (1, 2, 0, 1)]
+           (0, 2, 1, 2), (1, 2, 0, 1),
+           # f shells: every f pair class, f on the ket side, and (ff|ff)
+           (3, 0, 0, 0), (3, 1, 0, 0), (3, 2, 1, 0), (3, 3, 0, 0), (1, 0, 3, 2), (3, 1, 3, 1), (3, 3, 3, 3)]
 
 
 @pytest.mark.parametrize("cls", CLASSES)

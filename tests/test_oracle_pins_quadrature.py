@@ -98,9 +98,16 @@ def _spd_mol(seed):
                     [(s.atom, s.l, s.alpha, s.coef) for s in m.shells] + [extra])
 
 
-@pytest.mark.parametrize("seed", [3, 17])
-def test_pd_one_electron_vs_quadrature(seed):
+def _spdf_mol(seed):
+    # the s/p/d molecule plus a 2-primitive f shell on the first atom
     m = _spd_mol(seed)
+    return make_mol([(int(z), tuple(x)) for z, x in zip(m.Z, m.xyz)],
+                    [(s.atom, s.l, s.alpha, s.coef) for s in m.shells] + [(0, 3, (0.45, 1.3), (0.7, 0.4))])
+
+
+@pytest.mark.parametrize("seed,f", [(3, False), (17, False), (5, True)])
+def test_pd_one_electron_vs_quadrature(seed, f):
+    m = _spdf_mol(seed) if f else _spd_mol(seed)
     B = OracleBasis(m)
     Sq, Tq, Vq = _quadrature_onee(m)
     for name, got, ref in (("S", B.onee("S"), Sq), ("T", B.onee("T"), Tq), ("V", B.onee("V"), Vq)):
