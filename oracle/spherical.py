@@ -7,6 +7,8 @@ Gaussians.  The oracle builds the spherical functions of each shell from the
 defining polynomials of the real solid harmonics,
     l = 0: 1;  l = 1: x, y, z;
     l = 2: xy, yz, 2z^2 - x^2 - y^2, xz, x^2 - y^2   (m = -2 .. 2),
+    l = 3: y(3x^2 - y^2), xyz, y(4z^2 - x^2 - y^2), z(2z^2 - 3x^2 - 3y^2),
+           x(4z^2 - x^2 - y^2), z(x^2 - y^2), x(x^2 - 3y^2)   (m = -3 .. 3),
 written on its own unit-normalised Cartesian functions (a monomial x^i y^j z^k
 is its normalised component times sqrt((2i-1)!!(2j-1)!!(2k-1)!!) up to a
 common factor), and then rescales each spherical function to unit norm with
@@ -27,6 +29,11 @@ _POLY = {
     1: [{(1, 0, 0): 1.0}, {(0, 1, 0): 1.0}, {(0, 0, 1): 1.0}],
     2: [{(1, 1, 0): 1.0}, {(0, 1, 1): 1.0}, {(0, 0, 2): 2.0, (2, 0, 0): -1.0, (0, 2, 0): -1.0},
         {(1, 0, 1): 1.0}, {(2, 0, 0): 1.0, (0, 2, 0): -1.0}],
+    3: [{(2, 1, 0): 3.0, (0, 3, 0): -1.0}, {(1, 1, 1): 1.0},
+        {(0, 1, 2): 4.0, (2, 1, 0): -1.0, (0, 3, 0): -1.0},
+        {(0, 0, 3): 2.0, (2, 0, 1): -3.0, (0, 2, 1): -3.0},
+        {(1, 0, 2): 4.0, (3, 0, 0): -1.0, (1, 2, 0): -1.0},
+        {(2, 0, 1): 1.0, (0, 2, 1): -1.0}, {(3, 0, 0): 1.0, (1, 2, 0): -3.0}],
 }
 
 

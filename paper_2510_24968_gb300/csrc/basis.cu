@@ -15,6 +15,7 @@
 #include <numeric>
 
 #include "fsim_internal.h"
+#include "pairdata.cuh"
 
 namespace fsim {
 
@@ -56,93 +57,6 @@ static void boys_table(std::vector<double>& tab, int npts, double h) {
   }
 }
 
-// ---------------------------------------------------------------------------
-// Shell-pair data kernel: one thread per (pair, primitive pair).
-// ---------------------------------------------------------------------------
-__host__ __device__ constexpr double comp_norm(int l, int c) {
-  // 1/sqrt((2i-1)!!(2j-1)!!(2k-1)!!) for l <= 2: only the squares (x^2 etc.) differ from 1
-  return (cart_comp(l, c, 0) == 2 || cart_comp(l, c, 1) == 2 || cart_comp(l, c, 2) == 2) ? 0.57735026918962576451
-                                                                                           : 1.0;
-}
-
-template <int LA, int LB>
-__global__ void pair_data_kernel(int n, int ppmax, const int4* __restrict__ idx, const double* __restrict__ cen,
-                                 const double* __restrict__ alpha, const double* __restrict__ coef,
-                                 const int* __restrict__ nprim, double* __restrict__ pd64,
-                                 float* __restrict__ pd32, double4_32a* __restrict__ pq64, float4* __restrict__ pq32) {
-  using PC = PairCls<LA, LB>;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n * ppmax) return;
-  const int j = t % n, k = t / n;
-  const int4 pi = idx[j];
-  const int sa = pi.z, sb = pi.w;
-  const int Ka = nprim[sa], Kb = nprim[sb];
-  const size_t fs = (size_t)ppmax * n;
-  auto put = [&](int f, double v) {
-    pd64[f * fs + (size_t)k * n + j] = v;
-    pd32[f * fs + (size_t)k * n + j] = (float)v;
-  };
-  if (k >= Ka * Kb) {
-    pq64[(size_t)k * n + j] = make_double4_32a(1.0, 0.0, 0.0, 0.0);
-    pq32[(size_t)k * n + j] = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
-    put(0, 1.0);
-    put(1, 0.0); put(2, 0.0); put(3, 0.0);
-    for (int z = 0; z < PC::NNZ; ++z) put(4 + z, 0.0);
-    return;
-  }
-  const int ka = k / Kb, kb = k % Kb;
-  const double a = alpha[sa * kMaxPrim + ka], b = alpha[sb * kMaxPrim + kb];
-  const double p = a + b, mu = a * b / p;
-  double E[3][LA + 1][LB + 1][LA + LB + 1];
-  double P[3];
-#pragma unroll
-  for (int x = 0; x < 3; ++x) {
-    const double A = cen[3 * sa + x], B = cen[3 * sb + x];
-    P[x] = (a * A + b * B) / p;
-    const double XAB = A - B, XPA = P[x] - A, XPB = P[x] - B, i2p = 0.5 / p;
-#pragma unroll
-    for (int i = 0; i <= LA; ++i)
-#pragma unroll
-      for (int jj = 0; jj <= LB; ++jj)
-#pragma unroll
-        for (int tt = 0; tt <= LA + LB; ++tt) E[x][i][jj][tt] = 0.0;
-    E[x][0][0][0] = exp(-mu * XAB * XAB);
-#pragma unroll
-    for (int i = 1; i <= LA; ++i)
-#pragma unroll
-      for (int tt = 0; tt <= i; ++tt)
-        E[x][i][0][tt] = (tt > 0 ? i2p * E[x][i - 1][0][tt - 1] : 0.0) + XPA * E[x][i - 1][0][tt] +
-                         (tt + 1 <= i - 1 ? (tt + 1) * E[x][i - 1][0][tt + 1] : 0.0);
-#pragma unroll
-    for (int jj = 1; jj <= LB; ++jj)
-#pragma unroll
-      for (int i = 0; i <= LA; ++i)
-#pragma unroll
-        for (int tt = 0; tt <= i + jj; ++tt)
-          E[x][i][jj][tt] = (tt > 0 ? i2p * E[x][i][jj - 1][tt - 1] : 0.0) + XPB * E[x][i][jj - 1][tt] +
-                            (tt + 1 <= i + jj - 1 ? (tt + 1) * E[x][i][jj - 1][tt + 1] : 0.0);
-  }
-  // sqrt(2) pi^{5/4} / p folds half of 2 pi^{5/2} / (p q) into each pair
-  const double scale = coef[sa * kMaxPrim + ka] * coef[sb * kMaxPrim + kb] * 1.41421356237309504880 *
-                       4.18251339837959907596 /* pi^{5/4} */ / p;
-  put(0, p);
-  put(1, P[0]); put(2, P[1]); put(3, P[2]);
-  pq64[(size_t)k * n + j] = make_double4_32a(p, P[0], P[1], P[2]);
-  pq32[(size_t)k * n + j] = make_float4((float)p, (float)P[0], (float)P[1], (float)P[2]);
-  static_for<PC::NC>([&](auto Aa) {
-    constexpr int ac = decltype(Aa)::value;
-    constexpr int ia = ac / PC::NB, ib = ac % PC::NB;
-    constexpr int ix = cart_comp(LA, ia, 0), iy = cart_comp(LA, ia, 1), iz = cart_comp(LA, ia, 2);
-    constexpr int jx = cart_comp(LB, ib, 0), jy = cart_comp(LB, ib, 1), jz = cart_comp(LB, ib, 2);
-    const double f = scale * comp_norm(LA, ia) * comp_norm(LB, ib);
-    static_for<PC::nnz(ac)>([&](auto Kk) {
-      constexpr int kk = decltype(Kk)::value;
-      constexpr int tt = PC::nz_t(ac, kk), uu = PC::nz_u(ac, kk), vv = PC::nz_v(ac, kk);
-      put(4 + PC::off(ac) + kk, f * E[0][ix][jx][tt] * E[1][iy][jy][uu] * E[2][iz][jz][vv]);
-    });
-  });
-}
-
 static cudaError_t launch_pair_data(int cls, int n, int ppmax, const int4* idx, const fsim_basis* b, double* pd64,
                                     float* pd32, double4_32a* pq64, float4* pq32) {
   const int total = n * ppmax, th = 128, bl = (total + th - 1) / th;
@@ -153,7 +67,8 @@ static cudaError_t launch_pair_data(int cls, int n, int ppmax, const int4* idx, 
     case 2: pair_data_kernel<1, 1><<<bl, th>>>(n, ppmax, idx, b->d_cen, b->d_alpha, b->d_coef, b->d_nprim, pd64, pd32, pq64, pq32); break;
     case 3: pair_data_kernel<2, 0><<<bl, th>>>(n, ppmax, idx, b->d_cen, b->d_alpha, b->d_coef, b->d_nprim, pd64, pd32, pq64, pq32); break;
     case 4: pair_data_kernel<2, 1><<<bl, th>>>(n, ppmax, idx, b->d_cen, b->d_alpha, b->d_coef, b->d_nprim, pd64, pd32, pq64, pq32); break;
-    default: pair_data_kernel<2, 2><<<bl, th>>>(n, ppmax, idx, b->d_cen, b->d_alpha, b->d_coef, b->d_nprim, pd64, pd32, pq64, pq32); break;
+    case 5: pair_data_kernel<2, 2><<<bl, th>>>(n, ppmax, idx, b->d_cen, b->d_alpha, b->d_coef, b->d_nprim, pd64, pd32, pq64, pq32); break;
+    default: return launch_pair_data_f(cls, n, ppmax, idx, b, pd64, pd32, pq64, pq32);
   }
   return cudaGetLastError();
 }
@@ -239,11 +154,12 @@ int ensure_dfloat(fsim_basis* b) {
 // One-electron integrals: one block per ordered shell pair, one thread per
 // Cartesian component pair.  Runtime loops (not on the hot path).
 // ---------------------------------------------------------------------------
-__device__ void herm_E_axis(double (&E)[3][5][7], int la, int lb, double a, double b, double XAB) {
+// E^{ij}_t of one axis for i <= la <= 3, j <= lb <= 5 (the kinetic term raises j by 2)
+__device__ void herm_E_axis(double (&E)[4][6][9], int la, int lb, double a, double b, double XAB) {
   const double p = a + b, mu = a * b / p, XPA = -b * XAB / p, XPB = a * XAB / p, i2p = 0.5 / p;
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 5; ++j)
-      for (int t = 0; t < 7; ++t) E[i][j][t] = 0.0;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 6; ++j)
+      for (int t = 0; t < 9; ++t) E[i][j][t] = 0.0;
   E[0][0][0] = exp(-mu * XAB * XAB);
   for (int i = 1; i <= la; ++i)
     for (int t = 0; t <= i; ++t)
@@ -276,7 +192,7 @@ __global__ void onee_kernel(int which, int nshell, const int* __restrict__ lsh, 
   for (int ka = 0; ka < nprim[sa]; ++ka)
     for (int kb = 0; kb < nprim[sb]; ++kb) {
       const double a = alpha[sa * kMaxPrim + ka], b = alpha[sb * kMaxPrim + kb], p = a + b;
-      double E[3][3][5][7];
+      double E[3][4][6][9];
       double P[3];
       for (int x = 0; x < 3; ++x) {
         herm_E_axis(E[x], la, lb + (which == 1 ? 2 : 0), a, b, cen[3 * sa + x] - cen[3 * sb + x]);
@@ -298,10 +214,10 @@ __global__ void onee_kernel(int which, int nshell, const int* __restrict__ lsh, 
         const int L = la + lb;
         for (int nuc = 0; nuc < natom; ++nuc) {
           const double X = P[0] - axyz[3 * nuc], Y = P[1] - axyz[3 * nuc + 1], Z = P[2] - axyz[3 * nuc + 2];
-          double F[5];
-          boys_fp64<4>(p * (X * X + Y * Y + Z * Z), F, boys + 4, kBoysCols);
+          double F[7];
+          boys_fp64<6>(p * (X * X + Y * Y + Z * Z), F, boys + 6, kBoysCols);
           // R^n_{tuv} for n + t + u + v <= L: level arrays, highest n first
-          double R[5][35];
+          double R[7][84];
           for (int n = L; n >= 0; --n) {
             double fac = 1.0;
             for (int m = 0; m < n; ++m) fac *= -2.0 * p;
@@ -335,7 +251,7 @@ int onee_device(fsim_basis* b, int which, double* d_out, cudaStream_t s) {
     set_error("fsim_onee: which must be 0 (S), 1 (T) or 2 (V)");
     return FSIM_EINVAL;
   }
-  onee_kernel<<<b->nshell * b->nshell, 64, 0, s>>>(which, b->nshell, b->d_l, b->d_nprim, b->d_ao, b->d_cen,
+  onee_kernel<<<b->nshell * b->nshell, 128, 0, s>>>(which, b->nshell, b->d_l, b->d_nprim, b->d_ao, b->d_cen,
                                                     b->d_alpha, b->d_coef, b->natom, b->d_axyz, b->d_Z, b->d_boys64,
                                                     b->nbf, d_out);
   FSIM_CK(cudaGetLastError());
@@ -348,7 +264,7 @@ int onee_device(fsim_basis* b, int which, double* d_out, cudaStream_t s) {
 static int compute_schwarz(fsim_basis* b) {
   const int ns = b->nshell;
   b->Q.assign((size_t)ns * ns, 0.0);
-  for (int X = 0; X < kNumPairCls; ++X) {
+  for (int X = 0; X < kNumPairClsAll; ++X) {
     DevClass& C = b->cls[X];
     if (C.n == 0) continue;
     const int nc = ncart(pair_cls_la(X)) * ncart(pair_cls_lb(X));
@@ -418,9 +334,9 @@ int fsim_basis_create_ex(const fsim_atom* atoms, int natom, const fsim_shell_des
   *out = nullptr;
   for (int s = 0; s < nshell; ++s) {
     const fsim_shell_desc& d = shells[s];
-    if (d.atom < 0 || d.atom >= natom || d.l < 0 || d.l > 2 || d.nprim < 1 || d.nprim > kMaxPrim || !d.alpha ||
+    if (d.atom < 0 || d.atom >= natom || d.l < 0 || d.l > 3 || d.nprim < 1 || d.nprim > kMaxPrim || !d.alpha ||
         !d.coef) {
-      set_error("fsim_basis_create: shell %d invalid (atom %d, l %d, nprim %d; need l<=2, 1<=nprim<=%d)", s, d.atom,
+      set_error("fsim_basis_create: shell %d invalid (atom %d, l %d, nprim %d; need l<=3, 1<=nprim<=%d)", s, d.atom,
                 d.l, d.nprim, kMaxPrim);
       return FSIM_EINVAL;
     }
@@ -498,7 +414,7 @@ int fsim_basis_create_ex(const fsim_atom* atoms, int natom, const fsim_shell_des
   }
 #undef UP
   // canonical pairs per class: higher l first; equal l: higher shell index first
-  std::vector<int4> order[kNumPairCls];
+  std::vector<int4> order[kNumPairClsAll];
   for (int sa = 0; sa < nshell; ++sa)
     for (int sb = 0; sb <= sa; ++sb) {
       int A = sa, B = sb;
@@ -506,7 +422,7 @@ int fsim_basis_create_ex(const fsim_atom* atoms, int natom, const fsim_shell_des
       const int X = pair_cls_index(b->sh_l[A], b->sh_l[B]);
       order[X].push_back(make_int4(b->sh_ao[A], b->sh_ao[B], A, B));
     }
-  for (int X = 0; X < kNumPairCls; ++X)
+  for (int X = 0; X < kNumPairClsAll; ++X)
     if ((rc = build_pair_data(b, X, order[X])) != FSIM_OK) return fail(rc);
   if (flags & FSIM_BASIS_SPHERICAL) {
     b->spherical = 1;

@@ -269,6 +269,10 @@ int fsim_batch_create(fsim_basis* const* bases, int nmol, const fsim_fock_opts* 
       set_error("fsim_batch_create: null entry for molecule %d", m);
       return fail(FSIM_EINVAL);
     }
+    if (has_f(b)) {
+      set_error("fsim_batch_create: molecule %d has f shells (batches serve s, p and d shells)", m);
+      return fail(FSIM_EINVAL);
+    }
     bt->b.push_back(b);
     if ((rc = ensure_schwarz(b)) != FSIM_OK || (rc = ensure_scratch(b)) != FSIM_OK) return fail(rc);
     bt->h_ptrs.push_back(MolPtrs{b->d_Jacc, b->d_Kacc, b->d_D32, D[m], J[m], K[m], b->nbf});

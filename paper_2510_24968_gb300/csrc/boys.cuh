@@ -30,7 +30,7 @@
 
 namespace fsim {
 
-constexpr int kBoysMaxN = 8;           // highest order needed: (dd|dd)
+constexpr int kBoysMaxN = 12;          // highest order needed: (ff|ff)
 constexpr int kBoysK64 = 8;            // Taylor terms, FP64
 constexpr int kBoysK32 = 5;            // Taylor terms, FP32
 constexpr int kBoysCols = kBoysMaxN + kBoysK64 + 1;  // orders stored per grid point
@@ -207,7 +207,8 @@ struct Boys<float> {
 template <>
 struct Boys<dfloat> {
   // slots 0..K-1: F_{L..L+K-1}; slot K: e^{-T_i}, kept in the table's last
-  // column, which no class order reaches (L + K - 1 <= 15 < kBoysCols - 1)
+  // column, which no class order of the double-float kernels (s/p/d, L <= 8)
+  // reaches (L + K - 1 <= 15 < kBoysCols - 1)
   static constexpr int K = kBoysK64, NROW = kBoysN64, NCOL = K + 1;
   static __host__ __device__ constexpr int col(int L, int c) { return c < K ? L + c : kBoysCols - 1; }
   template <int L>

@@ -13,6 +13,7 @@
 
 #include "coop.cuh"
 #include "fsim_internal.h"
+#include "generic.cuh"
 
 namespace fsim {
 
@@ -76,7 +77,21 @@ int run_list(fsim_basis* b, int X, int Y, const std::vector<int2>& items, double
   int2* d_items = nullptr;
   FSIM_TRY(dev_alloc(&d_items, items.size()));
   cudaError_t e = cudaMemcpy(d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && X >= kNumPairCls) {
+    GenParams<double> p{};
+    p.bra = b->cls[X].view<double>();
+    p.ket = b->cls[Y].view<double>();
+    p.la = pair_cls_la(X); p.lb = pair_cls_lb(X); p.lc = pair_cls_la(Y); p.ld = pair_cls_lb(Y);
+    p.same = X == Y;
+    p.list_mode = 1;
+    p.items = d_items;
+    p.nitems = (int)items.size();
+    p.out = d_out;
+    p.N = b->nbf;
+    p.boys = b->d_boys64;
+    p.boys64_T = INFINITY;
+    e = launch_gen<double>(p, s);
+  } else if (e == cudaSuccess) {
     CoopParams<double> p{};
     p.bra = b->cls[X].view<double>();
     p.ket = b->cls[Y].view<double>();
@@ -209,7 +224,58 @@ int get_plan(fsim_basis* b, double tau, int shard, int nshards, int precision, F
       cp.fp64 = precision == FSIM_DFLOAT && !dfloat_default(X, Y);
       P->nquartets += cp.nquartets;
     }
+  // class pairs with an f class: flattened screened (bra, ket) lists, one
+  // quartet per CTA of the generic kernel (FP64 in double-float builds)
+  for (int X = kNumPairCls; X < kNumPairClsAll; ++X)
+    for (int Y = 0; Y <= X; ++Y) {
+      ClassPairPlan& cp = P->cp[X][Y];
+      cp.nbra = b->cls[X].n;
+      if (b->cls[X].n == 0 || b->cls[Y].n == 0) continue;
+      std::vector<int> count;
+      cp.nquartets = screened_counts(b, X, Y, tau, shard, nshards, count);
+      FSIM_TRY(set_class_plan(b, X, Y, count, 1, 0, cp, 1, 1));
+      cp.fp64 = precision == FSIM_DFLOAT;
+      P->nquartets += cp.nquartets;
+    }
   *out = P;
+  return FSIM_OK;
+}
+
+// The class pairs with an f class, on stream s (their quartet counts are below
+// 2^31 by set_class_plan's check).
+template <typename Real>
+static int launch_f_pairs(fsim_basis* b, FockPlan* plan, const Real* Dr, float boys64_T, double* Jacc,
+                          double* Kacc, cudaStream_t s, const double* D64 = nullptr) {
+  for (int X = kNumPairClsAll - 1; X >= kNumPairCls; --X)
+    for (int Y = X; Y >= 0; --Y) {
+      const ClassPairPlan& cp = plan->cp[X][Y];
+      if (cp.nquartets == 0) continue;
+      cudaError_t e = cudaSuccess;
+      if constexpr (std::is_same<Real, dfloat>::value) {
+        return launch_f_pairs<double>(b, plan, D64, boys64_T, Jacc, Kacc, s);
+      } else {
+        GenParams<Real> p{};
+        p.bra = b->cls[X].view<Real>();
+        p.ket = b->cls[Y].view<Real>();
+        p.la = pair_cls_la(X); p.lb = pair_cls_lb(X); p.lc = pair_cls_la(Y); p.ld = pair_cls_lb(Y);
+        p.same = X == Y;
+        p.list_mode = 0;
+        p.prefix = cp.d_prefix;
+        p.nitems = (int)cp.nquartets;
+        p.N = b->nbf;
+        p.D = Dr;
+        p.J = Jacc;
+        p.K = Kacc;
+        p.boys = std::is_same<Real, double>::value ? (const Real*)b->d_boys64 : (const Real*)b->d_boys32;
+        p.boys64_T = boys64_T;
+        e = launch_gen<Real>(p, s);
+      }
+      ++b->last_launches;
+      if (e != cudaSuccess) {
+        set_error("J/K kernel for f class pair (%d|%d): %s", X, Y, cudaGetErrorString(e));
+        return FSIM_ECUDA;
+      }
+    }
   return FSIM_OK;
 }
 
@@ -354,12 +420,14 @@ static int launch_all(fsim_basis* b, FockPlan* plan, const Real* Dr, float boys6
         return FSIM_ECUDA;
       }
     }
+    FSIM_TRY(launch_f_pairs<Real>(b, plan, Dr, boys64_T, b->d_Jacc, b->d_Kacc, s, D64));
     for (int k = 1; k < nuse; ++k) {
       FSIM_CK(cudaEventRecord(b->join_ev[k - 1], st[k]));
       FSIM_CK(cudaStreamWaitEvent(s, b->join_ev[k - 1], 0));
     }
     return FSIM_OK;
   }
+  FSIM_TRY(launch_f_pairs<Real>(b, plan, Dr, boys64_T, b->d_Jacc, b->d_Kacc, s, D64));
   for (int X = kNumPairCls - 1; X >= 0; --X)
     for (int Y = X; Y >= 0; --Y) {
       const ClassPairPlan& cp = plan->cp[X][Y];
@@ -441,7 +509,7 @@ struct PairLoc {
 static std::vector<PairLoc> pair_locations(const fsim_basis* b) {
   const int ns = b->nshell;
   std::vector<PairLoc> loc((size_t)ns * ns, PairLoc{-1, -1, 0});
-  for (int X = 0; X < kNumPairCls; ++X)
+  for (int X = 0; X < kNumPairClsAll; ++X)
     for (int j = 0; j < b->cls[X].n; ++j) {
       const int A = b->cls[X].h_idx[j].z, B = b->cls[X].h_idx[j].w;
       loc[(size_t)A * ns + B] = PairLoc{X, j, 0};
@@ -529,7 +597,7 @@ int fsim_eri_quartets(fsim_basis* b, int n, const int* quartets, double* out, in
     int sw_bk;     // bra and ket swapped
     int sw1, sw2;  // stored pair order swapped (bra, ket as stored)
   };
-  std::vector<Req> groups[kNumPairCls][kNumPairCls];
+  std::vector<Req> groups[kNumPairClsAll][kNumPairClsAll];
   std::vector<size_t> out_off(n + 1, 0);
   for (int q = 0; q < n; ++q) {
     const int* s4 = quartets + 4 * q;
@@ -549,7 +617,7 @@ int fsim_eri_quartets(fsim_basis* b, int n, const int* quartets, double* out, in
     }
     groups[p1.cls][p2.cls].push_back(Req{q, p1.idx, p2.idx, sw, p1.swapped, p2.swapped});
   }
-  for (int X = 0; X < kNumPairCls; ++X)
+  for (int X = 0; X < kNumPairClsAll; ++X)
     for (int Y = 0; Y <= X; ++Y) {
       auto& G = groups[X][Y];
       if (G.empty()) continue;
@@ -665,7 +733,7 @@ static int launch_all_into(fsim_basis* b, FockPlan* plan, const Real* Dr, float 
         return FSIM_ECUDA;
       }
     }
-  return FSIM_OK;
+  return launch_f_pairs<Real>(b, plan, Dr, boys64_T, Jacc, Kacc, s);
 }
 
 int fock_build_into(fsim_basis* b, const double* dD, double* dJ, double* dK, const fsim_fock_opts& o, double* Jacc,

@@ -197,9 +197,16 @@ struct FockPlan {
   int precision = 0;
   int psplit_force = 0;
   bool tuned = false;
-  ClassPairPlan cp[kNumPairCls][kNumPairCls];
+  // s/p/d class pairs at [X][Y], X, Y < kNumPairCls; the class pairs with an f
+  // class (X >= kNumPairCls) hold flattened quartet lists for the generic kernel
+  ClassPairPlan cp[kNumPairClsAll][kNumPairClsAll];
   long long nquartets = 0;
 };
+
+template <typename Real>
+struct GenParams;
+template <typename Real>
+cudaError_t launch_gen(const GenParams<Real>& p, cudaStream_t s);
 
 // Kernel launchers (explicit instantiations in eri_inst_*.cu).
 template <typename Real, int X, int Y>
@@ -240,7 +247,7 @@ struct fsim_basis {
   int* d_ao = nullptr;
   double* d_axyz = nullptr;
   int* d_Z = nullptr;
-  fsim::DevClass cls[fsim::kNumPairCls];
+  fsim::DevClass cls[fsim::kNumPairClsAll];
   bool schwarz_done = false;
   std::vector<double> Q;  // nshell x nshell
   double* d_boys64 = nullptr;
@@ -299,6 +306,8 @@ int ensure_scratch(fsim_basis* b);
 int noalloc_scratch_prepare();
 int ensure_schwarz(fsim_basis* b);
 int ensure_aux_streams(fsim_basis* b);
+// true when the basis has f shells (class pairs served by the generic kernel)
+inline bool has_f(const fsim_basis* b);
 // input, hidden and output widths of a network handle (mlp.cu)
 void mlp_dims(const fsim_mlp* net, int* nin, int* width, int* nout);
 int device_sm_count();
@@ -312,3 +321,9 @@ int onee_ext_device(fsim_basis* b, int which, double* out, cudaStream_t s);
 int sph_setup(fsim_basis* b);
 int onee_device(fsim_basis* b, int which, double* d_out, cudaStream_t s);
 }  // namespace fsim
+
+inline bool fsim::has_f(const fsim_basis* b) {
+  for (int X = kNumPairCls; X < kNumPairClsAll; ++X)
+    if (b->cls[X].n > 0) return true;
+  return false;
+}

@@ -267,6 +267,10 @@ extern "C" int fsim_j_build(fsim_basis* b, const double* D, double* J, const fsi
     set_error("fsim_j_build: spherical bases are not supported (use fsim_fock_build)");
     return FSIM_EINVAL;
   }
+  if (has_f(b)) {
+    set_error("fsim_j_build: bases with f shells are not supported (use fsim_fock_build)");
+    return FSIM_EINVAL;
+  }
   fsim_fock_opts o;
   fsim_fock_opts_default(&o);
   if (opts) o = *opts;

@@ -64,22 +64,29 @@ struct PairCls {
   __host__ __device__ static constexpr int nz_v(int a, int k) { return k % (ext(a, 2) + 1); }
 };
 
-// Runtime-visible sizes of the six pair classes ss, ps, pp, ds, dp, dd.
+// Pair classes: the six s/p/d classes ss, ps, pp, ds, dp, dd (indices 0..5,
+// served by the compile-time kernels) and the four f classes fs, fp, fd, ff
+// (6..9, served by the runtime-angular-momentum kernel of generic.cuh).
 constexpr int kNumPairCls = 6;
+constexpr int kNumPairClsAll = 10;
 __host__ __device__ constexpr int pair_cls_index(int la, int lb) {
-  return la == 0 ? 0 : (la == 1 ? (lb == 0 ? 1 : 2) : (lb == 0 ? 3 : (lb == 1 ? 4 : 5)));
+  return la == 3 ? 6 + lb
+                 : (la == 0 ? 0 : (la == 1 ? (lb == 0 ? 1 : 2) : (lb == 0 ? 3 : (lb == 1 ? 4 : 5))));
 }
-__host__ __device__ constexpr int pair_cls_la(int c) { return c == 0 ? 0 : (c <= 2 ? 1 : 2); }
+__host__ __device__ constexpr int pair_cls_la(int c) { return c >= 6 ? 3 : (c == 0 ? 0 : (c <= 2 ? 1 : 2)); }
 __host__ __device__ constexpr int pair_cls_lb(int c) {
-  return c == 0 ? 0 : (c == 1 ? 0 : (c == 2 ? 1 : (c == 3 ? 0 : (c == 4 ? 1 : 2))));
+  return c >= 6 ? c - 6 : (c == 0 ? 0 : (c == 1 ? 0 : (c == 2 ? 1 : (c == 3 ? 0 : (c == 4 ? 1 : 2)))));
 }
+// non-zero E^{ab}_{tuv} over the Cartesian components of a pair class
 __host__ __device__ constexpr int pair_cls_nnz(int c) {
-  return c == 0 ? PairCls<0, 0>::NNZ
-       : c == 1 ? PairCls<1, 0>::NNZ
-       : c == 2 ? PairCls<1, 1>::NNZ
-       : c == 3 ? PairCls<2, 0>::NNZ
-       : c == 4 ? PairCls<2, 1>::NNZ
-                : PairCls<2, 2>::NNZ;
+  const int la = pair_cls_la(c), lb = pair_cls_lb(c);
+  int s = 0;
+  for (int a = 0; a < ncart(la) * ncart(lb); ++a) {
+    int e = 1;
+    for (int x = 0; x < 3; ++x) e *= cart_comp(la, a / ncart(lb), x) + cart_comp(lb, a % ncart(lb), x) + 1;
+    s += e;
+  }
+  return s;
 }
 
 }  // namespace fsim

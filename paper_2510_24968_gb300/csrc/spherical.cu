@@ -59,7 +59,68 @@ __global__ void cart_from_sph_kernel(const double* __restrict__ in, int ns, doub
 
 }  // namespace
 
+// An f shell (Cartesian order xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz) gives,
+// for m = -3 .. 3, the real solid harmonics
+//   y(3x^2 - y^2), xyz, y(4z^2 - x^2 - y^2), z(2z^2 - 3x^2 - 3y^2),
+//   x(4z^2 - x^2 - y^2), z(x^2 - y^2), x(x^2 - 3y^2),
+// written on the unit-normalised components (a monomial x^i y^j z^k is its
+// component times sqrt((2i-1)!!(2j-1)!!(2k-1)!!), up to the shell's common
+// radial factor) and scaled to unit norm with the components' overlap within
+// the shell, <a|b> = prod_axes (i_a + i_b - 1)!! / sqrt(prod (2i_a - 1)!! (2i_b - 1)!!)
+// (zero when an exponent sum is odd).
+namespace {
+double dfact_odd(int n) {  // n!! for odd n >= -1
+  double r = 1.0;
+  for (int k = n; k > 1; k -= 2) r *= k;
+  return r;
+}
+struct Mono {
+  int i, j, k;
+  double c;
+};
+void f_rows(std::vector<std::vector<std::pair<int, double>>>& rows) {
+  const std::vector<std::vector<Mono>> poly = {
+      {{2, 1, 0, 3.0}, {0, 3, 0, -1.0}},
+      {{1, 1, 1, 1.0}},
+      {{0, 1, 2, 4.0}, {2, 1, 0, -1.0}, {0, 3, 0, -1.0}},
+      {{0, 0, 3, 2.0}, {2, 0, 1, -3.0}, {0, 2, 1, -3.0}},
+      {{1, 0, 2, 4.0}, {3, 0, 0, -1.0}, {1, 2, 0, -1.0}},
+      {{2, 0, 1, 1.0}, {0, 2, 1, -1.0}},
+      {{3, 0, 0, 1.0}, {1, 2, 0, -3.0}}};
+  auto comp = [](int i, int j) {  // component index of (i, j, 3 - i - j) in the shell's order
+    int n = 0;
+    for (int a = 3; a >= 0; --a)
+      for (int b = 3 - a; b >= 0; --b) {
+        if (a == i && b == j) return n;
+        ++n;
+      }
+    return -1;
+  };
+  rows.clear();
+  for (const auto& P : poly) {
+    std::vector<Mono> t;
+    for (const Mono& m : P)
+      t.push_back(Mono{m.i, m.j, m.k, m.c * std::sqrt(dfact_odd(2 * m.i - 1) * dfact_odd(2 * m.j - 1) *
+                                                     dfact_odd(2 * m.k - 1))});
+    double n2 = 0.0;
+    for (const Mono& x : t)
+      for (const Mono& y : t) {
+        if ((x.i + y.i) % 2 || (x.j + y.j) % 2 || (x.k + y.k) % 2) continue;
+        const double ov = dfact_odd(x.i + y.i - 1) * dfact_odd(x.j + y.j - 1) * dfact_odd(x.k + y.k - 1) /
+                          std::sqrt(dfact_odd(2 * x.i - 1) * dfact_odd(2 * x.j - 1) * dfact_odd(2 * x.k - 1) *
+                                    dfact_odd(2 * y.i - 1) * dfact_odd(2 * y.j - 1) * dfact_odd(2 * y.k - 1));
+        n2 += x.c * y.c * ov;
+      }
+    std::vector<std::pair<int, double>> row;
+    for (const Mono& x : t) row.push_back({comp(x.i, x.j), x.c / std::sqrt(n2)});
+    rows.push_back(row);
+  }
+}
+}  // namespace
+
 int sph_setup(fsim_basis* b) {
+  std::vector<std::vector<std::pair<int, double>>> frows;
+  f_rows(frows);
   const double h = 0.5, r3 = std::sqrt(3.0) / 2.0;
   std::vector<int> ti, ci((size_t)b->nbf * 2, 0);
   std::vector<double> tc, cc((size_t)b->nbf * 2, 0.0);
@@ -82,6 +143,11 @@ int sph_setup(fsim_basis* b) {
     const int c0 = b->sh_ao[s];
     if (b->sh_l[s] < 2) {
       for (int k = 0; k < ncart(b->sh_l[s]); ++k) add(i++, c0 + k, 1.0);
+    } else if (b->sh_l[s] == 3) {
+      for (const auto& row : frows) {
+        for (const auto& e : row) add(i, c0 + e.first, e.second);
+        ++i;
+      }
     } else {  // xx 0, xy 1, xz 2, yy 3, yz 4, zz 5
       add(i, c0 + 1, 1.0);
       ++i;

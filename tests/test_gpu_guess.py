@@ -196,6 +196,8 @@ def test_adam_step_from_combined_shares_equals_train_step():
         torch.cuda.synchronize()
     # Adam's first steps move each parameter by about lr times the sign of its
     # gradient, so a component whose gradient rounds across zero can differ by
-    # 2 lr: compare the whole update in norm
+    # up to 2 lr per step; every other component agrees to rounding (~1e-7 of
+    # the 3e-3 updates): at most 0.2 % of the parameters may disagree
     da, db = net.params() - p0, twin.params() - p0
-    assert np.linalg.norm(da - db) < 1e-2 * np.linalg.norm(da)
+    assert np.mean(np.abs(da - db) > 1e-5) < 2e-3
+    assert np.linalg.norm(da - db) < 3e-2 * np.linalg.norm(da)

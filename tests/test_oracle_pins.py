@@ -508,6 +508,24 @@ def test_spherical_d_shell_orthonormal_and_free_of_r2():
         off += n
 
 
+def test_spherical_f_shell_orthonormal_and_free_of_r2_p():
+    # the seven f functions of a shell are orthonormal (only their norms are imposed)
+    # and none overlaps a p shell on the same atom; the Cartesian f shell holds
+    # r^2 x, r^2 y, r^2 z, which do overlap it (x^3 and xyy here)
+    from oracle import SphericalOracleBasis
+    mol = make_mol([(8, (0.0, 0.0, 0.0)), (1, (0.0, 1.1, 1.4))],
+                   [(0, 0, (0.3, 1.2), (0.6, 0.5)), (0, 1, (0.4, 1.5), (0.5, 0.7)),
+                    (0, 3, (0.5, 1.4), (0.8, 0.3)), (1, 0, (0.5,), (1.0,))])
+    B = SphericalOracleBasis(mol)
+    assert B.nbf == B.nbf_cart - 3
+    S, Sc = B.onee("S"), B.cart.onee("S")
+    fs, ps = 1 + 3, 1  # spherical offsets: s, p, f, s
+    assert np.abs(S[fs:fs + 7, fs:fs + 7] - np.eye(7)).max() < 1e-13
+    assert np.abs(S[ps:ps + 3, fs:fs + 7]).max() < 1e-13
+    fc = int(B.cart.ao[2])
+    assert abs(Sc[ps, fc + 0]) > 0.05 and abs(Sc[ps, fc + 3]) > 0.01  # <x|xxx>, <x|xyy>
+
+
 def test_spherical_equals_cartesian_without_d():
     from oracle import OracleBasis, SphericalOracleBasis
     from fsim_synth import workload
