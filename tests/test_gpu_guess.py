@@ -175,29 +175,28 @@ def test_frames_features_blocks_match_oracle(k, seed):
 
 
 def test_adam_step_from_combined_shares_equals_train_step():
-    # data-parallel update on one device: the gradients of two shares of a
-    # minibatch, combined with their mask sums, then fsim_mlp_adam_step, give the
-    # same parameters as fsim_mlp_train_step on the whole minibatch
+    # data-parallel update on one device, its two halves checked sharply:
+    # (1) the gradients of two shares of a minibatch, weighted by their mask sums,
+    #     are the whole minibatch's gradient (FP32 GEMMs: to rounding);
+    # (2) fsim_mlp_adam_step fed the whole minibatch's gradient takes the same step
+    #     as fsim_mlp_train_step (same BF16 kernels, same gradient)
     from paper_2510_24968_gb300.guess import GuessNet
     net, x, t, m = _net_and_data(width=64, b=512, seed=4)
     twin = GuessNet(width=64, seed=5)
     assert np.array_equal(twin.params(), net.params())
     xd, td, md = (torch.from_numpy(a).cuda() for a in (x, t, m))
-    p0 = net.params().astype(np.float64)
+    _, gfull = net.grad(xd.data_ptr(), td.data_ptr(), md.data_ptr(), 512, bf16=False)
+    num, den = 0.0, 0.0
+    for sl in (slice(0, 200), slice(200, 512)):
+        xs, ts, ms = xd[sl].contiguous(), td[sl].contiguous(), md[sl].contiguous()
+        _, g = net.grad(xs.data_ptr(), ts.data_ptr(), ms.data_ptr(), ms.shape[0], bf16=False)
+        w = float(ms.sum().item())
+        num, den = num + g.astype(np.float64) * w, den + w
+    assert np.linalg.norm(num / den - gfull) < 1e-5 * np.linalg.norm(gfull)
     for step in range(3):
+        _, g = twin.grad(xd.data_ptr(), td.data_ptr(), md.data_ptr(), 512, bf16=True)
+        twin.adam_step(g, 1e-3)
         net.train_step(xd.data_ptr(), td.data_ptr(), md.data_ptr(), 512, 1e-3)
-        num, den = 0.0, 0.0
-        for sl in (slice(0, 200), slice(200, 512)):
-            xs, ts, ms = xd[sl].contiguous(), td[sl].contiguous(), md[sl].contiguous()
-            _, g = twin.grad(xs.data_ptr(), ts.data_ptr(), ms.data_ptr(), ms.shape[0], bf16=True)
-            w = float(ms.sum().item())
-            num, den = num + g.astype(np.float64) * w, den + w
-        twin.adam_step((num / den).astype(np.float32), 1e-3)
         torch.cuda.synchronize()
-    # Adam's first steps move each parameter by about lr times the sign of its
-    # gradient, so a component whose gradient rounds across zero can differ by
-    # up to 2 lr per step; every other component agrees to rounding (~1e-7 of
-    # the 3e-3 updates): at most 0.2 % of the parameters may disagree
-    da, db = net.params() - p0, twin.params() - p0
-    assert np.mean(np.abs(da - db) > 1e-5) < 2e-3
-    assert np.linalg.norm(da - db) < 3e-2 * np.linalg.norm(da)
+    pa, pb = net.params(), twin.params()
+    assert np.abs(pa - pb).max() <= 1e-6 * max(1.0, np.abs(pa).max())
