@@ -30,7 +30,7 @@ extern "C" {
 #endif
 
 #define FSIM_OK 0
-#define FSIM_EINVAL (-1)          /* bad argument (null pointer, size, l > 2, ...) */
+#define FSIM_EINVAL (-1)          /* bad argument (null pointer, size, l > 3, ...) */
 #define FSIM_ECUDA (-2)           /* a CUDA runtime / library call failed */
 #define FSIM_ENOCONV (-3)         /* SCF hit max_iter; the result struct is still filled */
 #define FSIM_EILLCOND (-4)        /* overlap matrix (near) singular: min eigenvalue < 1e-10 */
@@ -78,7 +78,7 @@ typedef struct {
  * that S_mumu = 1.  Builds the shell-pair data (Gaussian product theorem,
  * Sec. 2.1.2; Hermite coefficients E^{ij}_t of Eqs. recurrence-A/B, collapsed
  * per Eq. E-tuv) on the device.  *out receives a new handle.
- * Errors: FSIM_EINVAL for bad sizes or l > 2 or nprim outside 1..4,
+ * Errors: FSIM_EINVAL for bad sizes or l > 3 or nprim outside 1..4,
  * FSIM_ECUDA / FSIM_ENOMEM from the device.
  */
 int fsim_basis_create(const fsim_atom* atoms, int natom, const fsim_shell_desc* shells, int nshell,
@@ -88,7 +88,11 @@ int fsim_basis_create(const fsim_atom* atoms, int natom, const fsim_shell_desc* 
  * The same with flags.  FSIM_BASIS_SPHERICAL: the basis the caller sees is the
  * real solid-harmonic one of Sec. 2.1.1 (2l+1 functions per shell: s; p in x, y,
  * z order; d as m = -2..2: xy, yz, z^2 - (x^2+y^2)/2, xz, (sqrt 3/2)(x^2 - y^2)
- * on the unit-normalised Cartesian components, each unit-normalised).  The
+ * on the unit-normalised Cartesian components, each unit-normalised; f as
+ * m = -3..3: y(3x^2 - y^2), xyz, y(4z^2 - x^2 - y^2), z(2z^2 - 3x^2 - 3y^2),
+ * x(4z^2 - x^2 - y^2), z(x^2 - y^2), x(x^2 - 3y^2), each unit-normalised).
+ * Shells up to f (l = 3) in every build path except fsim_j_build, batches and
+ * the learned guess, which refuse bases with f shells (FSIM_EINVAL).  The
  * integrals are still evaluated over Cartesian shells; fsim_onee,
  * fsim_fock_build and fsim_scf take and return matrices in the spherical basis
  * (D_cart = T^T D T before the build, J = T J_cart T^T after).  fsim_eri_quartets

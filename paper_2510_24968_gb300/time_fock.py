@@ -37,6 +37,8 @@ def main(argv=None):
     ap.add_argument("--scf", action="store_true", help="also run the SCF to convergence")
     ap.add_argument("--spherical", action="store_true", help="real solid-harmonic basis")
     ap.add_argument("--jengine", action="store_true", help="also time Coulomb-only J-engine builds")
+    ap.add_argument("--dw-screen", action="store_true", help="SCF: density-weighted screening of the increments")
+    ap.add_argument("--skip-builds", action="store_true", help="only the SCF (with --scf)")
     a = ap.parse_args(argv)
 
     mol = workload(a.workload)
@@ -56,6 +58,9 @@ def main(argv=None):
     for prec in precs:
         name = {FSIM_MIXED: "mixed", FSIM_FP64: "fp64", FSIM_DFLOAT: "dfloat"}[prec]
         kw = dict(tau=a.tau, precision=prec, boys_fp64_T=a.boys_fp64_T)
+        if a.skip_builds and a.scf:
+            out[name] = {"scf": _scf(gb, prec, a)}
+            continue
         if a.tune:
             tuned = gb.autotune(tau=a.tau, precision=prec)
             out[f"{name}_autotune"] = {f"{_NAMES[x]}|{_NAMES[y]}": c for (x, y), (c, _) in tuned.items()}
@@ -91,11 +96,27 @@ def main(argv=None):
             out[name]["jengine_ms"] = tj
             out[name]["jengine_ordered_quartets"] = gb.last_quartet_count()
         if a.scf:
-            t0 = time.perf_counter()
-            r = gb.scf(precision=prec, tau=a.tau)
-            out[name]["scf"] = {"e_total": r["e_total"], "iters": r["iters"], "converged": bool(r["converged"]),
-                                "wall_s": time.perf_counter() - t0}
+            out[name]["scf"] = _scf(gb, prec, a)
     print(json.dumps(out))
+
+
+def _scf(gb, prec, a):
+    """SCF to convergence; time from the start of the call until the energy stays
+    within 1e-8 Eh of the run's own converged energy (set-up and guess included)."""
+    t0 = time.perf_counter()
+    r = gb.scf(precision=prec, tau=a.tau, dw_screen=a.dw_screen, max_iter=150)
+    wall = time.perf_counter() - t0
+    E, T = r["energies"], r["times"]
+    setup = wall - r["time_s"]
+    tte = None
+    for i in range(len(E)):
+        if all(abs(e - r["e_total"]) < 1e-8 for e in E[i:]):
+            tte = float(T[i]) + setup
+            break
+    return {"e_total": r["e_total"], "iters": r["iters"], "converged": bool(r["converged"]), "wall_s": wall,
+            "setup_s": setup, "time_to_1e-8_of_final_s": tte, "fp64_accurate_builds": r["fp64_builds"],
+            "mixed_builds": r["mixed_builds"], "quartets": r["quartets"], "dw_screen": a.dw_screen,
+            "energies": [float(e) for e in E], "times": [float(t) for t in T]}
 
 
 if __name__ == "__main__":

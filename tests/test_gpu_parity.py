@@ -227,7 +227,7 @@ def test_jk_edge_cases():
 
 def test_invalid_arguments_raise():
     from paper_2510_24968_gb300 import Basis, FsimError
-    bad = make_mol([(1, (0.0, 0.0, 0.0))], [(0, 3, (0.5,), (1.0,))])
+    bad = make_mol([(1, (0.0, 0.0, 0.0))], [(0, 4, (0.5,), (1.0,))])  # g shells are not supported
     with pytest.raises(FsimError):
         Basis(bad)
     gb = Basis(workload("water"))
