@@ -362,6 +362,7 @@ def cloud60_section(args, gb_dev, sptr, flush):
     e1.record(torch.cuda.current_stream())
     torch.cuda.synchronize()
     ms_j = e0.elapsed_time(e1)
+    nq_j = gb.last_quartet_count()
     _, t_df, q_df = one(FSIM_DFLOAT, shard=0, nshards=CLOUD_SHARDS)
     ms_df = sum(t_df.values())
     nq_df = sum(q_df.values())
@@ -374,7 +375,7 @@ def cloud60_section(args, gb_dev, sptr, flush):
         "mixed_fp64_boys_T30": {"ms_serialised": ms_b64, "eri_quartets_per_s_serialised": nq / (ms_b64 * 1e-3),
                                 "fock_builds_per_s_serialised": 1e3 / ms_b64,
                                 "vs_fp32_boys_serialised": ms_b64 / ms_mx_ser},
-        "j_engine_mixed": {"ms": ms_j, "vs_fused_jk": ms_j / ms_mx, "ordered_quartets": gb.last_quartet_count()},
+        "j_engine_mixed": {"ms": ms_j, "vs_fused_jk": ms_j / ms_mx, "ordered_quartets": nq_j},
         "fp64_accurate_shard": {"precision": "double-float kernels up to L = 4, FP64 kernels above",
                                 "shard": f"0 of {CLOUD_SHARDS} (bra pairs i % {CLOUD_SHARDS} == 0)",
                                 "ms": ms_df, "unique_quartets": nq_df,
