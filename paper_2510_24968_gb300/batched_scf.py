@@ -68,9 +68,22 @@ def main(argv=None):
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--no-fp64-reset", action="store_true", help="mixed without the final FP64 builds")
     ap.add_argument("--dw-screen", action="store_true", help="density-weighted screening of the increments")
+    ap.add_argument("--indices", default=None,
+                    help="comma-separated members of the set to run (per-molecule rows are printed)")
     a = ap.parse_args(argv)
 
     mols = batched_set(a.nmol, seed=a.seed, nmin=a.nmin, nmax=a.nmax)
+    if a.indices:
+        idx = [int(x) for x in a.indices.split(",")]
+        prec = FSIM_MIXED if a.precision == "mixed" else FSIM_FP64
+        bases = [Basis(mols[i]) for i in idx]
+        res = scf_batched(bases, precision=prec, tau=a.tau, final_fp64=not a.no_fp64_reset, max_iter=a.max_iter,
+                          dw_screen=a.dw_screen)
+        for i, b, r in zip(idx, bases, res):
+            print(json.dumps({"index": i, "nbf": b.nbf, "converged": r["converged"], "iters": r["iters"],
+                              "e_total": r["e_total"], "last_de": float(np.abs(np.diff(r["energies"][-3:])).max())
+                              if len(r["energies"]) > 2 else None}))
+        return
     import os
     if int(os.environ.get("WORLD_SIZE", 1)) > 1:
         return main_sharded(a, mols)
