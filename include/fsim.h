@@ -307,7 +307,15 @@ typedef struct {
   int mixed_builds;     /* Fock builds done in mixed precision */
   double guess_s;       /* wall time of the initial density (prediction and check for a learned or
                            supplied guess, core-H diagonalisation otherwise), inside the set-up */
+  int mixed_fallback;   /* 1: FSIM_MIXED was requested, but the overlap's smallest eigenvalue is below
+                           FSIM_MIXED_MIN_S_EIG: in so nearly linearly dependent a basis the density has
+                           large elements, and FP32 integral errors multiplied by them exceed the mixed
+                           path's 1e-6 Eh bound, so every build ran FP64-accurate (FSIM_DFLOAT when
+                           final_fp64 = 2, else FSIM_FP64) */
 } fsim_scf_result;
+
+/* Smallest overlap eigenvalue for which fsim_scf / fsim_scf_batched run FSIM_MIXED builds. */
+#define FSIM_MIXED_MIN_S_EIG 1e-4
 
 /*
  * Restricted Hartree-Fock SCF (Sec. 3.2): core-Hamiltonian (or supplied)
@@ -345,7 +353,8 @@ void fsim_batch_destroy(fsim_batch* batch);
  * group as each molecule's state requires) and the per-molecule FP64 linear
  * algebra spread over several streams; converged molecules drop out.  Same
  * options and per-molecule semantics as fsim_scf (core-H guess only; FSIM_FP64
- * or FSIM_MIXED; each molecule's electron count is its nuclear charge).  results: nmol entries;
+ * or FSIM_MIXED, the FP64-accurate fallback of FSIM_MIXED_MIN_S_EIG decided per molecule; each
+ * molecule's electron count is its nuclear charge).  results: nmol entries;
  * time_s is the time from the start of the iteration loop (after the set-up:
  * one-electron matrices, orthogonaliser, guess, batch plans) at which that
  * molecule converged; t_hist counts from the same point.

@@ -403,6 +403,8 @@ struct Mol {
   std::vector<double> cv;
   long long quartets = 0;
   int n64 = 0, nmx = 0;
+  bool mixed = false;  // this molecule's builds are mixed (else FP64-accurate throughout)
+  double smin = 0.0;   // smallest overlap eigenvalue
 };
 
 int gemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, double alpha,
@@ -599,6 +601,13 @@ extern "C" int fsim_scf_batched(fsim_basis* const* bases, int nmol, const fsim_s
     FSIM_TRY(density_from(m, ln, m.H, m.D));
   }
   FSIM_TRY(join());
+  // per molecule: mixed builds only when the overlap is well enough conditioned
+  FSIM_CK(cudaStreamSynchronize(s0));
+  for (auto& m : mols) {
+    FSIM_CK(cudaMemcpy(&m.smin, m.w, sizeof(double), cudaMemcpyDeviceToHost));  // eigenvalues ascending
+    m.mixed = mixed && m.smin >= FSIM_MIXED_MIN_S_EIG;
+    m.phase = m.mixed ? 0 : 2;  // without mixed builds there is no settling phase
+  }
   // ---- the batch: Din -> J, K for every molecule
   {
     std::vector<const double*> Din(nmol);
@@ -621,7 +630,7 @@ extern "C" int fsim_scf_batched(fsim_basis* const* bases, int nmol, const fsim_s
       Mol& m = mols[i];
       act64[i] = actmx[i] = 0;
       if (m.conv) continue;
-      m.want64 = !mixed || (m.phase == 2 && o.final_fp64 && !m.have_G);
+      m.want64 = !m.mixed || (m.phase == 2 && o.final_fp64 && !m.have_G);
       m.incr = o.incremental && m.have_G && !m.want64;
       if (m.incr)
         b_add<<<blocks(m.n2), th, 0, s0>>>(m.D, m.Dn, -1.0, m.Din, m.n2);
@@ -655,7 +664,7 @@ extern "C" int fsim_scf_batched(fsim_basis* const* bases, int nmol, const fsim_s
       } else {
         b_add<<<blocks(n2), th, 0, ln.s>>>(m.J, m.K, -0.5, m.G, n2);
         m.have_G = true;
-        if (mixed && m.want64) {
+        if (m.mixed && m.want64) {
           FSIM_CK(cudaMemcpyAsync(m.Dr, m.D, sizeof(double) * n2, cudaMemcpyDeviceToDevice, ln.s));
           ++m.nresets;
         }
@@ -711,7 +720,7 @@ extern "C" int fsim_scf_batched(fsim_basis* const* bases, int nmol, const fsim_s
       FSIM_CK(cudaMemcpyAsync(m.Dn, m.D, sizeof(double) * m.n2, cudaMemcpyDeviceToDevice, ln.s));
       FSIM_TRY(density_from(m, ln, Fuse, m.D));
       b_dot<<<64, 256, 0, ln.s>>>(m.D, m.Dn, m.n2, slots + (size_t)i * kSlots + 1, 1);
-      if (mixed && o.final_fp64) b_dot<<<64, 256, 0, ln.s>>>(m.Dn, m.Dr, m.n2, slots + (size_t)i * kSlots + 2, 1);
+      if (m.mixed && o.final_fp64) b_dot<<<64, 256, 0, ln.s>>>(m.Dn, m.Dr, m.n2, slots + (size_t)i * kSlots + 2, 1);
     }
     FSIM_TRY(join());
     FSIM_CK(cudaMemcpyAsync(hs.data(), slots, sizeof(double) * nmol * kSlots, cudaMemcpyDeviceToHost, s0));
@@ -738,7 +747,7 @@ extern "C" int fsim_scf_batched(fsim_basis* const* bases, int nmol, const fsim_s
         continue;
       }
       if (m.phase == 2 && dE < o.conv_dE && rmsD < o.conv_dD) {
-        if (mixed && o.final_fp64 && m.nresets < 6 && std::sqrt(hs[(size_t)i * kSlots + 2] / (double)m.n2) > 1e-6) {
+        if (m.mixed && o.final_fp64 && m.nresets < 6 && std::sqrt(hs[(size_t)i * kSlots + 2] / (double)m.n2) > 1e-6) {
           m.have_G = false;
           m.have_old = false;
           continue;
@@ -760,7 +769,8 @@ extern "C" int fsim_scf_batched(fsim_basis* const* bases, int nmol, const fsim_s
     r.converged = m.conv ? 1 : 0;
     r.guess_fallback = 0;
     r.time_s = m.conv ? m.t_conv : total;
-    r.min_s_eig = 0.0;
+    r.min_s_eig = m.smin;
+    r.mixed_fallback = mixed && !m.mixed;
     r.quartets = 0;
     r.fp64_builds = m.n64;
     r.mixed_builds = m.nmx;

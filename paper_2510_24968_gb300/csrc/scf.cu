@@ -291,6 +291,7 @@ int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res) {
   double smin = 0.0;
   FSIM_CK(cudaMemcpy(&smin, eg.w, sizeof(double), cudaMemcpyDeviceToHost));
   res->min_s_eig = smin;
+  res->mixed_fallback = 0;
   if (!(smin > 1e-10)) {
     set_error("fsim_scf: overlap matrix ill-conditioned (min eigenvalue %.3e)", smin);
     return FSIM_EILLCOND;
@@ -383,10 +384,14 @@ int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res) {
 
   fsim_fock_opts fo = o.fock;
   fo.ptr_mode = FSIM_PTR_DEVICE;
-  const bool mixed = o.fock.precision == FSIM_MIXED;
+  // mixed builds only in a basis whose overlap is well enough conditioned for
+  // FP32 integrals (FSIM_MIXED_MIN_S_EIG); otherwise every build FP64-accurate
+  const bool mixed_req = o.fock.precision == FSIM_MIXED;
+  const bool mixed = mixed_req && smin >= FSIM_MIXED_MIN_S_EIG;
+  res->mixed_fallback = mixed_req && !mixed;
   // precision of the FP64-accurate builds: the requested one, or on the mixed
   // path the resets' (FP64, or double-float with final_fp64 == 2)
-  const int prec64 = !mixed ? o.fock.precision : (o.final_fp64 == 2 ? FSIM_DFLOAT : FSIM_FP64);
+  const int prec64 = !mixed_req ? o.fock.precision : (o.final_fp64 == 2 ? FSIM_DFLOAT : FSIM_FP64);
   // phase 0: mixed settling; phase 2: final accuracy.  With final_fp64 each
   // FP64 build resets G; the iteration only stops once the density has not
   // moved (rms 1e-6) since the last reset, so the FP32 part of G is tiny.

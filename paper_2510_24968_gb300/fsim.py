@@ -77,7 +77,7 @@ class fsim_scf_result(C.Structure):
                 ("converged", C.c_int), ("guess_fallback", C.c_int), ("D_out", C.POINTER(C.c_double)),
                 ("e_hist", C.POINTER(C.c_double)), ("t_hist", C.POINTER(C.c_double)), ("time_s", C.c_double),
                 ("min_s_eig", C.c_double), ("quartets", C.c_longlong), ("fp64_builds", C.c_int),
-                ("mixed_builds", C.c_int), ("guess_s", C.c_double)]
+                ("mixed_builds", C.c_int), ("guess_s", C.c_double), ("mixed_fallback", C.c_int)]
 
 
 _lib = None
@@ -363,7 +363,8 @@ class Basis:
                 "converged": bool(r.converged), "rc": rc, "time_s": r.time_s, "min_s_eig": r.min_s_eig,
                 "quartets": r.quartets, "fp64_builds": r.fp64_builds, "mixed_builds": r.mixed_builds,
                 "energies": eh[:n].copy(), "times": th[:n].copy(), "D": Dout,
-                "guess_fallback": bool(r.guess_fallback), "guess_s": r.guess_s}
+                "guess_fallback": bool(r.guess_fallback), "guess_s": r.guess_s,
+                "mixed_fallback": bool(r.mixed_fallback)}
 
 
 class Batch:
@@ -423,5 +424,6 @@ def scf_batched(bases, precision=FSIM_MIXED, tau=1e-10, max_iter=100, conv_dE=1e
     rc = _check(load().fsim_scf_batched(hb, n, C.byref(o), res), allow=(FSIM_ENOCONV,))
     return [{"e_total": r.e_total, "iters": r.iters, "converged": bool(r.converged), "time_s": r.time_s,
              "fp64_builds": r.fp64_builds, "mixed_builds": r.mixed_builds, "rc": rc,
+             "mixed_fallback": bool(r.mixed_fallback), "min_s_eig": r.min_s_eig,
              "energies": h[:r.iters].copy(), "times": t[:r.iters].copy(), "D": d}
             for r, h, t, d in zip(res, hist, thist, dens)]

@@ -167,3 +167,35 @@ def test_scf_batched_config3_samples_match_oracle():
         if r["converged"]:
             assert x["converged"], r["index"]
             assert abs(x["e_total"] - r["e_total"]) < 1e-8, (r["index"], x["e_total"], r["e_total"])
+
+
+def test_mixed_falls_back_to_fp64_accurate_builds_in_near_dependent_bases():
+    # molecules 47 and 508 of the 512-molecule set have overlap eigenvalues
+    # 8.7e-5 and 5.2e-5 (below FSIM_MIXED_MIN_S_EIG = 1e-4): a FSIM_MIXED SCF
+    # runs FP64-accurate builds for them, flags it, and reaches the oracle's
+    # energy; water (6.6e-4) keeps its mixed builds
+    import json
+    import os
+    from paper_2510_24968_gb300 import FSIM_MIXED, Basis, scf_batched
+    from fsim_synth import water
+    gold = os.path.join(os.path.dirname(__file__), "golden", "config3_oracle.json")
+    if not os.path.exists(gold):
+        pytest.skip("tests/golden/config3_oracle.json not written yet (make_config3_oracle.py)")
+    with open(gold) as f:
+        g = json.load(f)
+    rows = [r for r in g["molecules"] if r["converged"]]
+    mols = batched_set(512)
+    bases = [Basis(mols[r["index"]]) for r in rows] + [Basis(water())]
+    smin = [np.linalg.eigvalsh(b.onee("S"))[0] for b in bases]
+    assert all(s < 1e-4 for s in smin[:-1]) and smin[-1] > 1e-4
+    res = scf_batched(bases, precision=FSIM_MIXED, tau=g["tau"], max_iter=g["max_iter"])
+    for r, x, b, s in zip(rows, res, bases, smin):
+        assert x["mixed_fallback"] and x["mixed_builds"] == 0, r["index"]
+        assert abs(x["min_s_eig"] - s) < 1e-12 * max(1.0, abs(s)) + 1e-15
+        assert x["converged"] and abs(x["e_total"] - r["e_total"]) < 1e-8, (r["index"], x["e_total"])
+        y = b.scf(precision=FSIM_MIXED, tau=g["tau"], max_iter=g["max_iter"])
+        assert y["mixed_fallback"] and y["mixed_builds"] == 0 and abs(y["min_s_eig"] - s) < 1e-12
+        assert y["converged"] and abs(y["e_total"] - r["e_total"]) < 1e-8, (r["index"], y["e_total"])
+    assert not res[-1]["mixed_fallback"] and res[-1]["mixed_builds"] > 0 and res[-1]["converged"]
+    yw = bases[-1].scf(precision=FSIM_MIXED, tau=g["tau"])
+    assert not yw["mixed_fallback"] and yw["mixed_builds"] > 0
