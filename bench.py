@@ -549,7 +549,8 @@ def run_ours(args):
                "dfloat_vs_fp64_eh": rdd["e_total"] - r64["e_total"],
                "fp64_iters": r64["iters"], "mixed_iters": rmx["iters"], "mixed_resets": rmx["fp64_builds"],
                "mixed_fp64_resets_iters": rfr["iters"], "mixed_fp64_resets_builds": rfr["fp64_builds"],
-               "mixed_vs_fp64_eh": rmx["e_total"] - r64["e_total"],
+               "mixed_vs_fp64_eh": rmx["e_total"] - r64["e_total"], "mixed_fallback": rmx["mixed_fallback"],
+               "min_s_eig": rmx["min_s_eig"],
                "mixed_fp64_resets_vs_fp64_eh": rfr["e_total"] - r64["e_total"], "e_total_fp64": r64["e_total"],
                "mixed_reset_builds": "double-float (mixed_fp64_resets_*: the same SCF with FP64 resets)"}
         gold = os.path.join(ROOT, "tests", "golden", "water8_scf_oracle.json")
