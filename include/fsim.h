@@ -209,16 +209,18 @@ int fsim_j_build(fsim_basis* b, const double* D, double* J, const fsim_fock_opts
 /*
  * Autotuner for the Fock-build launches of this basis and these options
  * (screening, precision, shard): for every class pair it times each launch
- * shape on the device -- the unrolled per-class kernel with the bra primitive
- * pairs split over psplit = 1, 3 or 9 threads and the ket-component chunks
- * shared out over csplit = 1, 2 or 4 warp groups (a CTA of 128 threads takes
- * 128 / csplit / psplit kets), and the warp-cooperative kernel (4 kets per
- * CTA) -- and keeps the fastest in the basis' cached plan, which later
- * fsim_fock_build calls with the same options use.  FSIM_DFLOAT: every shape
- * with the double-float kernel and with the FP64 kernel (both FP64-accurate),
- * no cooperative kernel.  choice (36 entries, optional): 10 * psplit + csplit
- * for the unrolled kernel (+ 100 when a double-float build runs the class pair
- * with the FP64 kernel), -1 for the cooperative kernel, 0 for class pairs
+ * shape on the device -- the unrolled per-class kernel with each quartet's
+ * primitive quartets split over psplit = 1, 3, 9 or 27 threads (bra primitive
+ * pairs first; 27 also splits the ket primitive pairs three ways) and the
+ * ket-component chunks shared out over csplit = 1, 2 or 4 warp groups (a CTA
+ * of 128 threads takes floor(128 / csplit / psplit) kets), and the
+ * warp-cooperative kernel (4 kets per CTA) -- and keeps the fastest in the
+ * basis' cached plan, which later fsim_fock_build calls with the same options
+ * use.  FSIM_DFLOAT: every shape with the double-float kernel and with the
+ * FP64 kernel (both FP64-accurate), no cooperative kernel.  choice (36
+ * entries, optional): 10 * psplit + csplit for the unrolled kernel (+ 1000
+ * when a double-float build runs the class pair with the FP64 kernel), -1 for
+ * the cooperative kernel, 0 for class pairs
  * without work; best_ms (36, optional): its median time.  Index X*6+Y as in
  * fsim_last_class_times.
  */
@@ -229,8 +231,9 @@ int fsim_autotune(fsim_basis* b, const fsim_fock_opts* opts, int* choice, float*
  * precision, shard), e.g. choices saved from an earlier fsim_autotune.
  * choice: 36 host ints in fsim_autotune's encoding; 0 leaves a class pair as
  * it is.  Errors (FSIM_EINVAL, plan unchanged for that and later class pairs):
- * psplit not 1/3/9 or above the class's primitive pairs, csplit not 1/2/4 or
- * above its ket chunks, the cooperative kernel with FSIM_DFLOAT, +100 outside
+ * psplit not 1/3/9 or above the bra class's primitive pairs (27: bra class
+ * below 9 or ket class below 3 primitive pairs), csplit not 1/2/4 or above its
+ * ket chunks, the cooperative kernel with FSIM_DFLOAT, +1000 outside
  * FSIM_DFLOAT, or the double-float kernel for (dd|dp) and (dd|dd).
  */
 int fsim_set_launch(fsim_basis* b, const fsim_fock_opts* opts, const int* choice);

@@ -546,6 +546,8 @@ extern "C" int fsim_scf_batched(fsim_basis* const* bases, int nmol, const fsim_s
   }
   double* slots = nullptr;
   FSIM_TRY(A(&slots, (size_t)nmol * kSlots));
+  double* d_smin = nullptr;  // smallest overlap eigenvalue per molecule
+  FSIM_TRY(A(&d_smin, (size_t)nmol));
   std::vector<double> hs((size_t)nmol * kSlots);
   for (auto& ln : lanes) {
     FSIM_CK(cudaStreamCreateWithFlags(&ln.s, cudaStreamNonBlocking));
@@ -595,6 +597,8 @@ extern "C" int fsim_scf_batched(fsim_basis* const* bases, int nmol, const fsim_s
       set_error("cusolverDnDsyevd failed (overlap)");
       return FSIM_ECUDA;
     }
+    // eigenvalues ascending; m.w is reused for the orbital energies below
+    FSIM_CK(cudaMemcpyAsync(d_smin + (&m - mols.data()), m.w, sizeof(double), cudaMemcpyDeviceToDevice, ln.s));
     FSIM_CK(cudaMemcpyAsync(m.t1, m.V, sizeof(double) * m.n2, cudaMemcpyDeviceToDevice, ln.s));
     b_scale_cols<<<blocks(m.n2), th, 0, ln.s>>>(m.t1, m.w, m.N);
     FSIM_TRY(gemm(ln.blas, CUBLAS_OP_N, CUBLAS_OP_T, m.N, m.N, m.N, 1.0, m.t1, m.N, m.V, m.N, 0.0, m.X, m.N));
@@ -603,8 +607,10 @@ extern "C" int fsim_scf_batched(fsim_basis* const* bases, int nmol, const fsim_s
   FSIM_TRY(join());
   // per molecule: mixed builds only when the overlap is well enough conditioned
   FSIM_CK(cudaStreamSynchronize(s0));
+  std::vector<double> smin_h(nmol);
+  FSIM_CK(cudaMemcpy(smin_h.data(), d_smin, sizeof(double) * nmol, cudaMemcpyDeviceToHost));
   for (auto& m : mols) {
-    FSIM_CK(cudaMemcpy(&m.smin, m.w, sizeof(double), cudaMemcpyDeviceToHost));  // eigenvalues ascending
+    m.smin = smin_h[&m - mols.data()];
     m.mixed = mixed && m.smin >= FSIM_MIXED_MIN_S_EIG;
     m.phase = m.mixed ? 0 : 2;  // without mixed builds there is no settling phase
   }

@@ -81,7 +81,8 @@ struct JKParams {
   int nmol;
   int nitems;                           // total work items
   int same;                             // bra class == ket class
-  int psplit;                           // bra primitive pairs split over this many threads
+  int psplit;                           // primitive quartets of a quartet split over this many threads
+                                        // (bra primitive pairs first, then ket primitive pairs)
   int csplit;                           // ket chunks shared out over this many thread groups (1, 2, 4)
   int bra_ppmax;                        // largest bra primitive-pair count (shared-memory size)
   const Real* __restrict__ boys;
@@ -157,6 +158,13 @@ struct KetChunks {
 // a and ket components c = ch*CS + cs < NC, accumulated in this thread's
 // shared-memory slots so[(a * CS + cs) * kJKThreads] (so the registers hold
 // only R, the chunk's W and its E non-zeros).  Bra data: accessor bra(field, pp).
+// The bstep threads of a quartet share its primitive quartets: with bstep <=
+// nppb each takes whole bra primitive pairs (b0, b0 + bstep, ...) and every ket
+// primitive pair; with more threads than bra primitive pairs the ket primitive
+// pairs are split ks = ceil(bstep / nppb) ways as well, thread b0 taking the
+// units u = b0, b0 + bstep, ... < nppb * ks, each unit one bra primitive pair
+// (u % nppb) with every ks-th ket primitive pair from u / nppb.  The caller sums
+// the bstep partial blocks.
 // The chunk index is a runtime value (uniform across the warp), so the Boys
 // function, the R recursion, the bra transform and the caller's digestion exist
 // once in the code; only the ket transform (and its loads of the chunk's E
@@ -176,14 +184,16 @@ __device__ __forceinline__ void quartet_chunk(Real* __restrict__ so, const BraAt
 #pragma unroll
   for (int x = 0; x < BC::NC * CS; ++x) so[x * kJKThreads] = Real(0);
   const size_t kstride = (size_t)ket.ppmax * ket.n;
-  for (int b = b0; b < nppb; b += bstep) {
+  const int ks = (bstep + nppb - 1) / nppb;
+  for (int u = b0; u < nppb * ks; u += bstep) {
+    const int b = u % nppb;
     const Real p = bra(0, b), Px = bra(1, b), Py = bra(2, b), Pz = bra(3, b);
     Real W[NH1][CS];
 #pragma unroll
     for (int h = 0; h < NH1; ++h)
 #pragma unroll
       for (int cs = 0; cs < CS; ++cs) W[h][cs] = Real(0);
-    for (int k = 0; k < nppk; ++k) {
+    for (int k = u / nppb; k < nppk; k += ks) {
       const Real* kp = ket.pd + (size_t)k * ket.n + j;
       const auto q4 = ket.pq[(size_t)k * ket.n + j];
       const Real q = q4.x, Qx = q4.y, Qy = q4.z, Qz = q4.w;

@@ -179,6 +179,14 @@ int set_class_plan(fsim_basis* b, int X, int Y, const std::vector<int>& count, i
   return FSIM_OK;
 }
 
+// psplit 1, 3, 9 up to the bra class's primitive pairs; 27 (a ket-primitive
+// split on top of nine bra threads) where the bra class has at least 9 and the
+// ket class at least 3 primitive pairs.
+static bool psplit_legal(const fsim_basis* b, int X, int Y, int ps) {
+  if (ps == 27) return b->cls[X].ppmax >= 9 && b->cls[Y].ppmax >= 3;
+  return (ps == 1 || ps == 3 || ps == 9) && ps <= b->cls[X].ppmax;
+}
+
 // Screened plan for (tau, shard, precision, psplit_force); cached on the basis.
 // psplit_force = 0: class pairs with few quartets split the bra primitive pairs
 // over several threads so that one launch still covers the device.
@@ -210,11 +218,12 @@ int get_plan(fsim_basis* b, double tau, int shard, int nshards, int precision, F
         if (psplit_force > 0) {
           ps = std::min(psplit_force, CX.ppmax);
         } else {
-          // few quartets: split bra primitive pairs, then ket chunks, until
-          // one launch has about two CTAs' worth of threads per SM
+          // few quartets: split the primitive quartets (bra primitive pairs,
+          // then ket primitive pairs), then the ket chunks, until one launch
+          // has about two CTAs' worth of threads per SM
           const long long target = (long long)device_sm_count() * 2 * kJKThreads;
-          for (int c : {3, 9})
-            if (cp.nquartets * ps < target && c <= CX.ppmax) ps = c;
+          for (int c : {3, 9, 27})
+            if (cp.nquartets * ps < target && psplit_legal(b, X, Y, c)) ps = c;
           const int nch = jk_chunks_precision(precision, X, Y);
           for (int c : {2, 4})
             if (cp.nquartets * ps * cs < target && c <= nch) cs = c;
@@ -824,9 +833,9 @@ static int autotune_impl(fsim_basis* b, FockPlan* plan, const Real* Dr, float b6
       // double-float builds: each shape with the double-float and with the FP64 kernel
       const int f64_lo = kDf && !dfloat_kernel(X, Y) ? 1 : 0, f64_hi = kDf ? 1 : 0;
       for (int f64 = f64_lo; f64 <= f64_hi; ++f64)
-        for (int ps : {1, 3, 9})
+        for (int ps : {1, 3, 9, 27})
           for (int cs : {1, 2, 4})
-            if (ps <= b->cls[X].ppmax && cs <= nch) cands.push_back({ps, 0, cs, f64});
+            if (psplit_legal(b, X, Y, ps) && cs <= nch) cands.push_back({ps, 0, cs, f64});
       if (!kDf) cands.push_back({1, 1, 1, 0});
       float best = 1e30f;
       Cand win = cands[0];
@@ -860,7 +869,7 @@ static int autotune_impl(fsim_basis* b, FockPlan* plan, const Real* Dr, float b6
       if (rc != FSIM_OK) break;
       rc = set_class_plan(b, X, Y, count, win.psplit, win.coop, cp, win.csplit, jk_flat<Real>());
       cp.fp64 = win.fp64;
-      if (choice) choice[ci] = win.coop ? -1 : 10 * win.psplit + win.csplit + 100 * win.fp64;
+      if (choice) choice[ci] = win.coop ? -1 : 10 * win.psplit + win.csplit + 1000 * win.fp64;
       if (best_ms) best_ms[ci] = best;
     }
   cudaEventDestroy(e0);
@@ -891,8 +900,8 @@ extern "C" int fsim_set_launch(fsim_basis* b, const fsim_fock_opts* opts, const 
       ClassPairPlan& cp = plan->cp[X][Y];
       if (c == 0 || cp.nquartets == 0) continue;
       const int coop = c == -1 ? 1 : 0;
-      const int f64 = c >= 100 ? 1 : 0, ps = coop ? 1 : (c % 100) / 10, cs = coop ? 1 : c % 10;
-      const bool ok = c >= -1 && c < 200 && (coop ? !df : ((ps == 1 || ps == 3 || ps == 9) && ps <= b->cls[X].ppmax &&
+      const int f64 = c >= 1000 ? 1 : 0, ps = coop ? 1 : (c % 1000) / 10, cs = coop ? 1 : c % 10;
+      const bool ok = c >= -1 && c < 2000 && (coop ? !df : (psplit_legal(b, X, Y, ps) &&
                                                           (cs == 1 || cs == 2 || cs == 4) &&
                                                           cs <= jk_chunks_precision(o.precision, X, Y))) &&
                       (!f64 || df) && (!df || f64 || dfloat_kernel(X, Y));

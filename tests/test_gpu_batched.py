@@ -137,7 +137,7 @@ def test_autotune_keeps_results():
     D = torch.from_numpy(d + d.T).cuda()
     J0, K0 = b.fock_build(D, tau=1e-10, precision=FSIM_MIXED)
     choice = b.autotune(tau=1e-10, precision=FSIM_MIXED)
-    shapes = {-1} | {10 * ps + cs for ps in (1, 3, 9) for cs in (1, 2, 4)}
+    shapes = {-1} | {10 * ps + cs for ps in (1, 3, 9, 27) for cs in (1, 2, 4)}
     assert choice and all(c in shapes for c, _ in choice.values())
     J1, K1 = b.fock_build(D, tau=1e-10, precision=FSIM_MIXED)
     torch.cuda.synchronize()

@@ -98,16 +98,18 @@ def test_jk_every_kernel_and_shape(prec_name):
     Jo, Ko, _ = ob.jk(D)
     tol = (lambda M: 2e-6 * np.abs(Jo).max()) if prec == FSIM_MIXED else (lambda M: 1e-10)
     pairs = [(x, y) for x in range(6) for y in range(x + 1)]
-    variants = [11, 31] + ([111, 131] if prec == FSIM_DFLOAT else [-1])
+    variants = [11, 31] + ([1011, 1031] if prec == FSIM_DFLOAT else [-1])
     for v in variants:
         ch = {}
         for (x, y) in pairs:
-            ch[(x, y)] = v if not (prec == FSIM_DFLOAT and x == 5 and y >= 4 and v < 100) else v + 100
+            ch[(x, y)] = v if not (prec == FSIM_DFLOAT and x == 5 and y >= 4 and v < 1000) else v + 1000
         gb.set_launch(ch, tau=0.0, precision=prec)
         J, K = gb.fock_build(D, tau=0.0, precision=prec)
         assert np.abs(J - Jo).max() < tol(J) and np.abs(K - Ko).max() < tol(K), v
     with pytest.raises(FsimError):
         gb.set_launch({(0, 0): 91}, tau=0.0, precision=prec)  # 9 threads > 4 primitive pairs
+    with pytest.raises(FsimError):
+        gb.set_launch({(5, 5): 271}, tau=0.0, precision=prec)  # 27 threads need 9 bra primitive pairs
     if prec == FSIM_DFLOAT:
         with pytest.raises(FsimError):
             gb.set_launch({(5, 5): 11}, tau=0.0, precision=prec)  # no double-float (dd|dd) kernel

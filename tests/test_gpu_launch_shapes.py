@@ -1,13 +1,16 @@
 """Parity of every launch shape of the hot J/K kernels, through the C-ABI.
 
-The autotuner may give each class pair any of nine shapes of the unrolled
-kernel -- its bra primitive pairs split over psplit = 1, 3 or 9 threads, its
-ket-component chunks shared out over csplit = 1, 2 or 4 warp groups -- or the
-warp-cooperative kernel.  Each is forced here through fsim_set_launch on
-every class pair up to (dd|dd) of a molecule with 3-primitive s, p and d
-shells (9 primitive pairs, so psplit = 9 is legal), in FP64 and in mixed
-precision, and J, K are compared element by element with the oracle's
-(Eq. fock): 1e-10 max-abs for FP64, 2e-6 of max|J| for mixed.
+The autotuner may give each class pair any of twelve shapes of the unrolled
+kernel -- each quartet's primitive quartets split over psplit = 1, 3, 9 or 27
+threads (bra primitive pairs first, 27 splitting the ket primitive pairs as
+well), its ket-component chunks shared out over csplit = 1, 2 or 4 warp
+groups -- or the warp-cooperative kernel.  Each is forced here through
+fsim_set_launch on every class pair up to (dd|dd) of a molecule with
+3-primitive s, p and d shells (9 primitive pairs, so psplit = 9 and 27 are
+legal), in FP64 and in mixed precision, and J, K are compared element by
+element with the oracle's (Eq. fock): 1e-10 max-abs for FP64, 2e-6 of max|J|
+for mixed.  A molecule whose shells have 1 to 4 primitives (1 to 16 primitive
+pairs per shell pair) runs the split shapes with ragged primitive counts.
 
 The 60-heavy-atom organic cloud (1140 functions) is also built whole in mixed
 precision through the hot kernel, with a density that lives on a handful of
@@ -60,7 +63,7 @@ def test_every_launch_shape_every_class_pair(spd3, prec_name):
     tol = 1e-10 if prec == FSIM_FP64 else 2e-6 * np.abs(Jo).max()
     gb.fock_build(D, tau=0.0, precision=prec)  # plan
     covered = {}
-    for ps, cs in itertools.product((1, 3, 9), (1, 2, 4)):
+    for ps, cs in itertools.product((1, 3, 9, 27), (1, 2, 4)):
         code = 10 * ps + cs
         took = []
         for xy in PAIRS:
@@ -78,8 +81,36 @@ def test_every_launch_shape_every_class_pair(spd3, prec_name):
     J, K = gb.fock_build(D, tau=0.0, precision=prec)
     assert np.abs(J - Jo).max() < tol and np.abs(K - Ko).max() < tol
     # every shape reached the heaviest class pair, where the bench's tuned shapes live
-    assert all((5, 5) in covered[10 * ps + cs] for ps in (1, 3, 9) for cs in (1, 2, 4))
+    assert all((5, 5) in covered[10 * ps + cs] for ps in (1, 3, 9, 27) for cs in (1, 2, 4))
     assert len(covered[11]) == len(PAIRS)
+
+
+@pytest.mark.parametrize("prec_name", ["fp64", "mixed"])
+def test_split_shapes_ragged_primitive_counts(prec_name):
+    from oracle import OracleBasis
+    from paper_2510_24968_gb300 import FSIM_FP64, FSIM_MIXED, Basis
+    from .helpers import make_mol
+    prec = {"fp64": FSIM_FP64, "mixed": FSIM_MIXED}[prec_name]
+    rng = np.random.default_rng(2027)
+    atoms, shells = [], []
+    for a in range(3):
+        atoms.append((int(rng.integers(1, 9)), tuple(rng.uniform(-1.6, 1.6, 3))))
+        for l in range(3):
+            for k in (1 + (a + l) % 4, 4 - (a + 2 * l) % 4):  # 1..4 primitives
+                al = tuple(sorted(rng.uniform(0.2, 2.5, k)))
+                shells.append((a, l, al, tuple(rng.uniform(0.2, 1.0, k))))
+    mol = make_mol(atoms, shells, "ragged")
+    gb, ob = Basis(mol), OracleBasis(mol)
+    D = np.random.default_rng(79).standard_normal((gb.nbf, gb.nbf))
+    D = D + D.T
+    Jo, Ko, _ = ob.jk(D)
+    tol = 1e-10 if prec == FSIM_FP64 else 2e-6 * np.abs(Jo).max()
+    gb.fock_build(D, tau=0.0, precision=prec)
+    for ps, cs in itertools.product((3, 9, 27), (1, 2, 4)):
+        gb.set_launch({xy: 10 * ps + cs for xy in PAIRS}, tau=0.0, precision=prec)
+        J, K = gb.fock_build(D, tau=0.0, precision=prec)
+        ej, ek = np.abs(J - Jo).max(), np.abs(K - Ko).max()
+        assert ej < tol and ek < tol, (ps, cs, ej, ek)
 
 
 def test_hot_kernel_blocks_full_size_organic_cloud():
