@@ -211,7 +211,8 @@ int fsim_j_build(fsim_basis* b, const double* D, double* J, const fsim_fock_opts
  * (screening, precision, shard): for every class pair it times each launch
  * shape on the device -- the unrolled per-class kernel with each quartet's
  * primitive quartets split over psplit = 1, 3, 9 or 27 threads (bra primitive
- * pairs first; 27 also splits the ket primitive pairs three ways) and the
+ * pairs first; 27 also splits the ket primitive pairs three ways, tried only
+ * for class pairs with fewer than 2 x 128 x SMs / 9 quartets) and the
  * ket-component chunks shared out over csplit = 1, 2 or 4 warp groups (a CTA
  * of 128 threads takes floor(128 / csplit / psplit) kets), and the
  * warp-cooperative kernel (4 kets per CTA) -- and keeps the fastest in the

@@ -5,7 +5,9 @@
 Draws `nmol` molecules with U{nmin..nmax} heavy atoms (fsim_synth.batched_set),
 runs fsim_scf_batched on them (mixed precision by default) and prints one JSON
 object: wall time, molecules/s, converged count, p50/p99 of the per-molecule
-times, the mean iteration count, the set-up inside the call (one-electron
+times (all molecules, and the converged ones), the mean iteration count, how
+many molecules ran FP64-accurate builds because their overlap's smallest
+eigenvalue is below FSIM_MIXED_MIN_S_EIG, the set-up inside the call (one-electron
 matrices, orthogonalisers, guesses, batch plans) and the length of each lockstep
 iteration.  Every step runs in libfsim.
 """
@@ -82,7 +84,8 @@ def main(argv=None):
         for i, b, r in zip(idx, bases, res):
             print(json.dumps({"index": i, "nbf": b.nbf, "converged": r["converged"], "iters": r["iters"],
                               "e_total": r["e_total"], "last_de": float(np.abs(np.diff(r["energies"][-3:])).max())
-                              if len(r["energies"]) > 2 else None}))
+                              if len(r["energies"]) > 2 else None, "min_s_eig": r["min_s_eig"],
+                              "mixed_fallback": r["mixed_fallback"]}))
         return
     import os
     if int(os.environ.get("WORLD_SIZE", 1)) > 1:
@@ -100,6 +103,7 @@ def main(argv=None):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     ts = sorted(r["time_s"] for r in res)
+    tc = sorted(r["time_s"] for r in res if r["converged"])
     # lockstep: every molecule still iterating shares the iteration end times
     th = max((r["times"] for r in res), key=len)
     print(json.dumps({
@@ -109,6 +113,10 @@ def main(argv=None):
         "setup_s": setup,
         "wall_s": wall, "molecules_per_s": a.nmol / wall, "converged": sum(r["converged"] for r in res),
         "p50_s": ts[len(ts) // 2], "p99_s": ts[min(len(ts) - 1, int(0.99 * len(ts)))],
+        "p50_converged_s": tc[len(tc) // 2] if tc else None,
+        "p99_converged_s": tc[min(len(tc) - 1, int(0.99 * len(tc)))] if tc else None,
+        "mixed_fallback": int(sum(r["mixed_fallback"] for r in res)),
+        "min_s_eig_p50": float(np.median([r["min_s_eig"] for r in res])),
         "mean_iters": float(np.mean([r["iters"] for r in res])),
         "fp64_builds": int(sum(r["fp64_builds"] for r in res)),
         "in_call_setup_s": wall - float(th[-1]) if len(th) else None,

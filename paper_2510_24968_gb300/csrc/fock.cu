@@ -218,11 +218,13 @@ int get_plan(fsim_basis* b, double tau, int shard, int nshards, int precision, F
         if (psplit_force > 0) {
           ps = std::min(psplit_force, CX.ppmax);
         } else {
-          // few quartets: split the primitive quartets (bra primitive pairs,
-          // then ket primitive pairs), then the ket chunks, until one launch
-          // has about two CTAs' worth of threads per SM
+          // few quartets: split the bra primitive pairs, then the ket chunks,
+          // until one launch has about two CTAs' worth of threads per SM (the
+          // ket-primitive split, psplit 27, is left to the autotuner: it
+          // repeats the bra transform per ket group and lost on every class
+          // pair timed but the smallest)
           const long long target = (long long)device_sm_count() * 2 * kJKThreads;
-          for (int c : {3, 9, 27})
+          for (int c : {3, 9})
             if (cp.nquartets * ps < target && psplit_legal(b, X, Y, c)) ps = c;
           const int nch = jk_chunks_precision(precision, X, Y);
           for (int c : {2, 4})
@@ -829,13 +831,17 @@ static int autotune_impl(fsim_basis* b, FockPlan* plan, const Real* Dr, float b6
       };
       std::vector<Cand> cands;
       const int nch = jk_chunks<Real>(X, Y);
+      // the ket-primitive split (psplit 27) is tried only where nine threads
+      // per quartet leave the device short of two CTAs per SM
+      const long long fill = (long long)device_sm_count() * 2 * kJKThreads;
       constexpr bool kDf = std::is_same<Real, dfloat>::value;
       // double-float builds: each shape with the double-float and with the FP64 kernel
       const int f64_lo = kDf && !dfloat_kernel(X, Y) ? 1 : 0, f64_hi = kDf ? 1 : 0;
       for (int f64 = f64_lo; f64 <= f64_hi; ++f64)
         for (int ps : {1, 3, 9, 27})
           for (int cs : {1, 2, 4})
-            if (psplit_legal(b, X, Y, ps) && cs <= nch) cands.push_back({ps, 0, cs, f64});
+            if (psplit_legal(b, X, Y, ps) && cs <= nch && (ps < 27 || cp.nquartets * 9 < fill))
+              cands.push_back({ps, 0, cs, f64});
       if (!kDf) cands.push_back({1, 1, 1, 0});
       float best = 1e30f;
       Cand win = cands[0];

@@ -39,6 +39,9 @@ def main(argv=None):
     ap.add_argument("--jengine", action="store_true", help="also time Coulomb-only J-engine builds")
     ap.add_argument("--dw-screen", action="store_true", help="SCF: density-weighted screening of the increments")
     ap.add_argument("--skip-builds", action="store_true", help="only the SCF (with --scf)")
+    ap.add_argument("--shape-sweep", default="",
+                    help="comma-separated class pairs (e.g. dd|dd,dd|dp): time each with every legal launch "
+                         "shape (median of 5 per-class timings), after the build timings")
     a = ap.parse_args(argv)
 
     mol = workload(a.workload)
@@ -97,7 +100,33 @@ def main(argv=None):
             out[name]["jengine_ordered_quartets"] = gb.last_quartet_count()
         if a.scf:
             out[name]["scf"] = _scf(gb, prec, a)
+        if a.shape_sweep and prec != FSIM_DFLOAT:
+            out[name]["shape_sweep_ms"] = _shape_sweep(gb, D, J, K, kw, a)
     print(json.dumps(out))
+
+
+def _shape_sweep(gb, D, J, K, kw, a):
+    """Per class pair: median per-class kernel time (ms) of each launch shape the
+    library accepts, keyed by fsim_autotune's encoding (10 * psplit + csplit, -1 the
+    cooperative kernel); the class pair is left at its fastest shape."""
+    from .fsim import FsimError
+    res = {}
+    for lab in a.shape_sweep.split(","):
+        xy = tuple(_NAMES.index(t) for t in lab.split("|"))
+        times = {}
+        for code in [-1] + [10 * ps + cs for ps in (1, 3, 9, 27) for cs in (1, 2, 4)]:
+            try:
+                gb.set_launch({xy: code}, tau=a.tau, precision=kw["precision"])
+            except FsimError:
+                continue
+            t = []
+            for _ in range(5):
+                gb.fock_build(D, J, K, timing=True, **kw)
+                t.append(gb.last_class_times()[0][xy])
+            times[str(code)] = round(sorted(t)[2], 4)
+        gb.set_launch({xy: int(min(times, key=times.get))}, tau=a.tau, precision=kw["precision"])
+        res[lab] = times
+    return res
 
 
 def _scf(gb, prec, a):
