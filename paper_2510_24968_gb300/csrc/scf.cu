@@ -263,8 +263,6 @@ int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res) {
   FSIM_TRY(mem.alloc(&tmp, n2)); FSIM_TRY(mem.alloc(&tmp2, n2)); FSIM_TRY(mem.alloc(&e, n2));
   FSIM_TRY(mem.alloc(&scratch, (size_t)(kDotCTAs + 1) * std::max(o.diis_size, 1)));
   FSIM_TRY(mem.alloc(&Dr, n2));  // density of the last FP64 build (mixed path)
-  double* Gr = nullptr;           // its FP64-accurate G (mixed path, incremental resets)
-  FSIM_TRY(mem.alloc(&Gr, n2));
   const int m = o.diis_size;
   double *Fh = nullptr, *Eh = nullptr;
   if (m > 0) {
@@ -411,60 +409,40 @@ int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res) {
   res->mixed_builds = 0;
   int it = 0;
   const double t_loop0 = elapsed();
-  // Density-weighted threshold for a build of the difference density dX:
-  // tau / max|dX|, rounded down to tau 2^k so that the cached plans stay few.
-  // Every quartet it skips adds less than tau to J and K.
-  auto dw_tau = [&](const double* dX, double* t_eff) -> int {
-    int imax = 0;
-    BLAS_CK(cublasIdamax(c.blas, (int)n2, dX, 1, &imax));
-    double dmax = 0.0;
-    FSIM_CK(cudaMemcpyAsync(&dmax, dX + (imax - 1), sizeof(double), cudaMemcpyDeviceToHost, c.s));
-    FSIM_CK(cudaStreamSynchronize(c.s));
-    dmax = std::fabs(dmax);
-    *t_eff = o.fock.schwarz_tau;
-    if (o.fock.schwarz_tau > 0.0 && dmax < 1.0)
-      *t_eff = dmax > 0.0 ? std::ldexp(o.fock.schwarz_tau, std::min(60, (int)std::floor(-std::log2(dmax))))
-                          : std::ldexp(o.fock.schwarz_tau, 60);
-    return FSIM_OK;
-  };
   for (it = 1; it <= o.max_iter; ++it) {
     // ---- G(D), full or incremental
     const bool want64 = !mixed || (phase == 2 && o.final_fp64 && !have_G);
     fo.precision = want64 ? prec64 : FSIM_MIXED;
     if (o.incremental && have_G && !want64) {
       add_kernel<<<bl, th, 0, c.s>>>(D, Dn, -1.0, dD, n2);  // dD = D - D_prev (Dn holds D_prev)
-      // density-weighted screening while the mixed iteration settles.  The
-      // skipped terms are each below tau but add up over the increments of G,
-      // so from the FP64-accurate reset on every build keeps the plain
-      // threshold and the reset removes what was skipped
-      if (o.dw_screen && phase == 0) FSIM_TRY(dw_tau(dD, &fo.schwarz_tau));
+      if (o.dw_screen && phase == 0) {
+        // density-weighted screening while the mixed iteration settles:
+        // threshold tau / max|dD|, rounded down to tau 2^k so that the cached
+        // plans stay few.  The skipped terms are each below tau but add up in
+        // the incrementally built G, so from the FP64-accurate reset on every
+        // build keeps the plain threshold and the reset removes what was skipped
+        int imax = 0;
+        BLAS_CK(cublasIdamax(c.blas, (int)n2, dD, 1, &imax));
+        double dmax = 0.0;
+        FSIM_CK(cudaMemcpyAsync(&dmax, dD + (imax - 1), sizeof(double), cudaMemcpyDeviceToHost, c.s));
+        FSIM_CK(cudaStreamSynchronize(c.s));
+        dmax = std::fabs(dmax);
+        double t_eff = o.fock.schwarz_tau;
+        if (o.fock.schwarz_tau > 0.0 && dmax < 1.0)
+          t_eff = dmax > 0.0 ? std::ldexp(o.fock.schwarz_tau, std::min(60, (int)std::floor(-std::log2(dmax))))
+                             : std::ldexp(o.fock.schwarz_tau, 60);
+        fo.schwarz_tau = t_eff;
+      }
       FSIM_TRY(fock_build_ext_device(b, dD, J, K, fo));
       fo.schwarz_tau = o.fock.schwarz_tau;
       add_kernel<<<bl, th, 0, c.s>>>(G, J, 1.0, G, n2);
       add_kernel<<<bl, th, 0, c.s>>>(G, K, -0.5, G, n2);
-    } else if (mixed && want64 && nresets > 0 && o.incremental) {
-      // a later FP64-accurate reset: G(D) = G(D_r) + G(D - D_r), D_r the
-      // density of the previous reset and G(D_r) its FP64-accurate G, the
-      // difference built FP64-accurate with the density-weighted threshold.
-      // One increment, so its skipped terms (each below tau) do not pile up
-      // over iterations, and the FP32 parts of G since the last reset are gone
-      add_kernel<<<bl, th, 0, c.s>>>(D, Dr, -1.0, dD, n2);
-      FSIM_TRY(dw_tau(dD, &fo.schwarz_tau));
-      FSIM_TRY(fock_build_ext_device(b, dD, J, K, fo));
-      fo.schwarz_tau = o.fock.schwarz_tau;
-      add_kernel<<<bl, th, 0, c.s>>>(Gr, J, 1.0, G, n2);
-      add_kernel<<<bl, th, 0, c.s>>>(G, K, -0.5, G, n2);
-      FSIM_CK(cudaMemcpyAsync(Gr, G, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c.s));
-      FSIM_CK(cudaMemcpyAsync(Dr, D, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c.s));
-      have_G = true;
-      ++nresets;
     } else {
       FSIM_TRY(fock_build_ext_device(b, D, J, K, fo));
       add_kernel<<<bl, th, 0, c.s>>>(J, K, -0.5, G, n2);
       have_G = true;
       if (mixed && want64) {
         FSIM_CK(cudaMemcpyAsync(Dr, D, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c.s));
-        FSIM_CK(cudaMemcpyAsync(Gr, G, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c.s));
         ++nresets;
       }
     }
