@@ -223,15 +223,15 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
-def cpu_sample(mol, seconds_target: float, tau: float):
-    """The oracle's J/K over a bounded sample of bra pairs: (quartets/s, desc, cores)."""
+def cpu_sample(mol, seconds_target: float, tau: float, stride0: int = 64, ob=None):
+    """The oracle's J/K over a bounded sample of bra pairs: (quartets/s, quartets, seconds, stride)."""
     import numpy as np
     from oracle import OracleBasis
-    ob = OracleBasis(mol)
+    ob = ob or OracleBasis(mol)
     D = np.random.default_rng(0).standard_normal((ob.nbf, ob.nbf)) * 0.05
     D = D + D.T
     Q = ob.schwarz()  # noqa: F841  (warms the oracle's Schwarz path like a first build)
-    stride = 64
+    stride = stride0
     t0 = time.perf_counter()
     _, _, nq = ob.jk_sample(D, tau, stride)
     dt = time.perf_counter() - t0
@@ -294,6 +294,81 @@ def run_reference(args):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
+
+def run_oracle_timings(args):
+    """--oracle-timings: the oracle (plain FP64 C J/K with OpenMP over bra pairs,
+    numpy SCF; test infrastructure) timed on this host's cores for the four
+    configurations.  Whole SCFs where they end in seconds; otherwise one J/K
+    build, or a bra-pair sample of one, scaled by the screened quartet count and
+    by the oracle's own SCF iteration count (tests/golden), each labelled as an
+    extrapolation.  One JSON line."""
+    import platform
+
+    import numpy as np
+    from fsim_synth import batched_set, workload
+    from oracle import OracleBasis, rhf
+    gold = os.path.join(ROOT, "tests", "golden")
+    out = {"impl": "oracle-timings", "cores": os.cpu_count(), "machine": platform.machine(),
+           "oracle": "plain C FP64 J/K (OpenMP over bra pairs), numpy SCF"}
+    # water, 13 functions: the whole RHF (one-electron matrices, J/K, DIIS)
+    t0 = time.perf_counter()
+    mol = workload("water")
+    ob = OracleBasis(mol)
+    S, H = ob.onee("S"), ob.onee("T") + ob.onee("V")
+    r = rhf(S, H, lambda d: ob.jk(d)[:2], mol.nelec, ob.enuc())
+    out["water"] = {"scf_s": time.perf_counter() - t0, "iters": r.iters, "e_total": r.e_total,
+                    "kind": "measured: whole SCF, unscreened"}
+    # (H2O)_8, tau 1e-10: a bra-pair sample of one build, scaled to the full
+    # screened build and to the oracle SCF's 17 iterations
+    mol = workload(WORKLOAD)
+    v, nq, dt, stride = cpu_sample(mol, 15.0, 1e-10)
+    nq_full = screened_quartets(mol, 1e-10)
+    with open(os.path.join(gold, "water8_scf_oracle.json")) as f:
+        it8 = json.load(f)["iters"]
+    out["water8"] = {"quartets_per_s": v, "sample": f"bra pairs ij % {stride} == 0: {nq} quartets in {dt:.1f} s",
+                     "build_s_extrapolated": nq_full / v, "scf_s_extrapolated": it8 * nq_full / v,
+                     "scf_iters": it8, "kind": "extrapolated from the sample"}
+
+    # 60-heavy-atom cloud, tau 1e-11: Schwarz bounds once, then bra-pair samples
+    # of one build (each sample call recomputes the bounds: their time is taken off)
+    mol = workload("cloud60")
+    ob = OracleBasis(mol)
+    D = np.random.default_rng(0).standard_normal((ob.nbf, ob.nbf)) * 0.05
+    D = D + D.T
+    t0 = time.perf_counter()
+    ob.schwarz()
+    t_q = time.perf_counter() - t0
+    stride = 40000
+    while True:
+        t0 = time.perf_counter()
+        _, _, nq = ob.jk_sample(D, 1e-11, stride)
+        dt = max(time.perf_counter() - t0 - t_q, 1e-3)
+        if dt >= 10.0 or stride <= 2000:
+            break
+        stride = max(2000, int(stride * max(dt, 0.5) / 20.0))
+    nq_full = screened_quartets(mol, 1e-11)
+    out["cloud60"] = {"schwarz_s": t_q, "quartets_per_s": nq / dt,
+                      "sample": f"bra pairs ij % {stride} == 0: {nq} quartets in {dt:.1f} s (Schwarz excluded)",
+                      "screened_quartets": nq_full, "build_s_extrapolated": nq_full * dt / nq,
+                      "kind": "extrapolated from the sample; the sampled pairs' class mix sets the rate"}
+    # 512-molecule set: one J/K build of each member whose oracle SCF converged
+    # (tests/golden/config3_oracle.json), scaled by that SCF's iteration count
+    with open(os.path.join(gold, "config3_oracle.json")) as f:
+        g3 = json.load(f)
+    mols = batched_set(512)
+    rows = []
+    for m in g3["molecules"]:
+        if not m["converged"]:
+            continue
+        obm = OracleBasis(mols[m["index"]])
+        Dm = np.eye(obm.nbf)
+        t0 = time.perf_counter()
+        _, _, nqm = obm.jk(Dm, tau=g3["tau"])
+        dt = time.perf_counter() - t0
+        rows.append({"index": m["index"], "nbf": obm.nbf, "build_s": dt, "quartets": nqm, "iters": m["iters"],
+                     "scf_s_extrapolated": dt * m["iters"]})
+    out["batched_set_sample"] = {"molecules": rows, "kind": "one measured build per molecule x its oracle SCF iterations"}
+    print(json.dumps(out), flush=True)
 
 def time_to_energy(res, e_ref, tol=1e-8):
     """Seconds until the energy stays within tol of e_ref for the rest of the run."""
@@ -634,7 +709,12 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-cloud60", action="store_true")
     ap.add_argument("--no-jengine", action="store_true")
+    ap.add_argument("--oracle-timings", action="store_true",
+                    help="time the CPU oracle on the host cores for all configurations (one JSON line), then exit")
     args = ap.parse_args()
+    if args.oracle_timings:
+        run_oracle_timings(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.gpus < 1:
