@@ -592,6 +592,12 @@ def run_ours(args):
     names = ["ss", "ps", "pp", "ds", "dp", "dd"]
     all_fl = sum(qcls[k] * method_flops_per_quartet(*k) for k in qcls)
     all_fl_dense = sum(qcls[k] * flops_per_quartet(*k) for k in qcls)
+    # primitive quartets and Cartesian integrals per build (every shell of the
+    # workload has NPRIM primitives, so a shell quartet holds NPRIM^4)
+    assert all(len(sh.alpha) == NPRIM for sh in mol.shells)
+    prim_q = sum(qcls.values()) * NPRIM ** 4
+    cart_ints = sum(qcls[k] * ncart(PAIR_L[k[0]][0]) * ncart(PAIR_L[k[0]][1]) * ncart(PAIR_L[k[1]][0]) *
+                    ncart(PAIR_L[k[1]][1]) for k in qcls)
     cloud = cloud60_section(args, gb_dev=dev, sptr=sptr, flush=flush) if rank == 0 and world == 1 \
         and not args.no_cloud60 else None
 
@@ -655,6 +661,11 @@ def run_ours(args):
         "unique_quartets_per_build": q_mixed,
         "fock_builds_per_s": {"mixed": 1e3 / ms_mixed, "fp64": 1e3 / ms_fp64, "dfloat": 1e3 / ms_df},
         "eri_quartets_per_s": {"mixed": value, "fp64": q_fp64 / (ms_fp64 * 1e-3), "dfloat": q_df / (ms_df * 1e-3)},
+        "primitive_quartets_per_s": {"mixed": prim_q / (ms_mixed * 1e-3), "fp64": prim_q / (ms_fp64 * 1e-3),
+                                     "dfloat": prim_q / (ms_df * 1e-3)},
+        "cartesian_integrals_per_s": {"mixed": cart_ints / (ms_mixed * 1e-3), "fp64": cart_ints / (ms_fp64 * 1e-3),
+                                      "dfloat": cart_ints / (ms_df * 1e-3)},
+        "per_build": {"unique_quartets": q_mixed, "primitive_quartets": prim_q, "cartesian_integrals": cart_ints},
         "class_ms_fp64_dfloat": {f"{names[k[0]]}|{names[k[1]]}": [round(sum(cls_fp64[k]) / len(cls_fp64[k]), 3),
                                                                   round(sum(cls_df[k]) / len(cls_df[k]), 3)]
                                  for k in cls_fp64 if k in cls_df},
