@@ -384,8 +384,11 @@ int fsim_guess_assemble(fsim_basis* b, const float* blocks, double* D, void* str
 /*
  * The network: three linear layers with SiLU (nin -> width -> width -> nout),
  * FP32 master weights with BF16 copies; forward and backward GEMMs on the
- * tensor cores (BF16 inputs, FP32 accumulation), Adam (beta 0.9/0.999, eps
- * 1e-8).  init_params: host array of fsim_mlp_nparams() floats laid out
+ * fifth-generation tensor cores (tcgen05.mma: BF16 inputs, FP32 accumulation
+ * in tensor memory), Adam (beta 0.9/0.999, eps 1e-8).  The BF16 calls
+ * (fsim_mlp_forward with bf16 != 0, fsim_mlp_grad with bf16 != 0,
+ * fsim_mlp_train_step) synchronise the stream before returning and return
+ * FSIM_ECUDA if a GEMM's MMAs did not complete within its bounded wait.  init_params: host array of fsim_mlp_nparams() floats laid out
  * W1 [nin x width], b1, W2 [width x width], b2, W3 [width x nout], b3 (row-major).
  * x, y, t, mask: device FP32 arrays (batch x nin / batch x nout).  loss =
  * sum(mask (y - t)^2) / sum(mask).  fsim_mlp_grad returns that loss and its

@@ -4,8 +4,9 @@
 //   z1 = x W1 + b1, h1 = silu(z1), z2 = h1 W2 + b2, h2 = silu(z2), y = h2 W3 + b3
 //   loss = sum(mask (y - t)^2) / sum(mask)
 // Weights are kept in FP32 (master, Adam state) with BF16 copies; the GEMMs run
-// on the tensor cores (mma.sync m16n8k16, BF16 x BF16 -> FP32 accumulation).
-// A plain FP32 GEMM path (no BF16 rounding) serves the gradient check.
+// on the fifth-generation tensor cores (tcgen05.mma, BF16 x BF16 -> FP32
+// accumulation in tensor memory, tc_gemm.cuh).  A plain FP32 GEMM path (no
+// BF16 rounding) serves the gradient check.
 // silu(z) = z s(z), s = logistic; silu'(z) = s(z) (1 + z (1 - s(z))).
 #include <cuda_bf16.h>
 
@@ -18,6 +19,7 @@
 #include <vector>
 
 #include "fsim_internal.h"
+#include "tc_gemm.cuh"
 
 struct fsim_mlp {
   int nin = 0, width = 0, nout = 0;
@@ -31,6 +33,7 @@ struct fsim_mlp {
   float *z1 = nullptr, *h1 = nullptr, *z2 = nullptr, *h2 = nullptr, *y = nullptr;
   float *dy = nullptr, *d1 = nullptr, *d2 = nullptr;
   float* scal = nullptr;  // [0] loss numerator, [1] mask sum
+  int* tc_err = nullptr;  // set by a tensor-core GEMM whose MMAs did not complete
   long step = 0;
 };
 
@@ -53,8 +56,9 @@ Off offsets(int nin, int w, int nout) {
 }
 
 // C[M x N] = op(A) op(B) (+ bias[N]), op(A) M x K, op(B) K x N, all row-major
-// FP32 in memory; tA: A stored K x M; tB: B stored N x K.  BF16 mode rounds both
-// operands to BF16 and uses mma.sync; otherwise FP32 FMAs.
+// FP32 in memory; tA: A stored K x M; tB: B stored N x K.  This kernel is the
+// plain FP32 path (FMAs, no BF16 rounding) of the gradient check; BF16 GEMMs
+// run on the tensor cores (tc_gemm_kernel).
 constexpr int TM = 64, TN = 64, TK = 16;
 
 __device__ __forceinline__ float ldA(const float* A, int M, int K, bool tA, int r, int k) {
@@ -67,105 +71,42 @@ __device__ __forceinline__ float ldB(const float* B, int K, int N, bool tB, int 
 }
 
 __global__ void __launch_bounds__(128) gemm_kernel(const float* __restrict__ A, const float* __restrict__ B,
-                                                   const __nv_bfloat16* __restrict__ Bb, float* __restrict__ C,
-                                                   const float* __restrict__ bias, int M, int N, int K, int tA,
-                                                   int tB, int bf16) {
-  __shared__ __nv_bfloat16 As[TM][TK + 8];
-  __shared__ __nv_bfloat16 Bs[TK][TN + 8];
+                                                   float* __restrict__ C, const float* __restrict__ bias, int M,
+                                                   int N, int K, int tA, int tB) {
   __shared__ float Af[TM][TK + 1];
   __shared__ float Bf[TK][TN + 1];
   const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;  // warp tile 32 x 32
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
+  const int tid = threadIdx.x;
+  // thread owns rows (tid / 4) * 2 .. +1 and columns (tid % 4) * 16 .. +15 of the tile (32 outputs)
+  const int rr = (tid >> 2) * 2, cc = (tid & 3) * 16;
   float accf[32];
 #pragma unroll
   for (int r = 0; r < 32; ++r) accf[r] = 0.0f;
   for (int k0 = 0; k0 < K; k0 += TK) {
     for (int x = tid; x < TM * TK; x += 128) {
       const int r = x / TK, k = x % TK;
-      const float a = ldA(A, M, K, tA, m0 + r, k0 + k);
-      if (bf16) As[r][k] = __float2bfloat16(a); else Af[r][k] = a;
+      Af[r][k] = ldA(A, M, K, tA, m0 + r, k0 + k);
     }
     for (int x = tid; x < TK * TN; x += 128) {
       const int k = x / TN, c = x % TN;
-      if (bf16) {
-        const bool ok = (k0 + k) < K && (n0 + c) < N;
-        Bs[k][c] = (Bb && !tB) ? (ok ? Bb[(size_t)(k0 + k) * N + n0 + c] : __float2bfloat16(0.0f))
-                               : __float2bfloat16(ldB(B, K, N, tB, k0 + k, n0 + c));
-      } else {
-        Bf[k][c] = ldB(B, K, N, tB, k0 + k, n0 + c);
-      }
+      Bf[k][c] = ldB(B, K, N, tB, k0 + k, n0 + c);
     }
     __syncthreads();
-    if (bf16) {
-      const int g = lane >> 2, t = lane & 3;
 #pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int r = wm + i * 16;
-        // A fragment (16 x 16, row-major): pairs along k
-        uint32_t a[4];
-        auto pack = [](__nv_bfloat16 lo, __nv_bfloat16 hi) {
-          return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-        };
-        a[0] = pack(As[r + g][t * 2], As[r + g][t * 2 + 1]);
-        a[1] = pack(As[r + g + 8][t * 2], As[r + g + 8][t * 2 + 1]);
-        a[2] = pack(As[r + g][t * 2 + 8], As[r + g][t * 2 + 9]);
-        a[3] = pack(As[r + g + 8][t * 2 + 8], As[r + g + 8][t * 2 + 9]);
+    for (int k = 0; k < TK; ++k)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int c = wn + j * 8;
-          uint32_t b[2];
-          b[0] = pack(Bs[t * 2][c + g], Bs[t * 2 + 1][c + g]);
-          b[1] = pack(Bs[t * 2 + 8][c + g], Bs[t * 2 + 9][c + g]);
-          asm volatile(
-              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-              "{%0,%1,%2,%3};\n"
-              : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
-              : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-        }
-      }
-    } else {
-      // FP32: thread owns rows (tid / 4) * 2 .. +1 and columns (tid % 4) * 16 .. +15 of the tile (32 outputs)
-      const int rr = (tid >> 2) * 2, cc = (tid & 3) * 16;
+      for (int i = 0; i < 2; ++i)
 #pragma unroll
-      for (int k = 0; k < TK; ++k)
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-          for (int j = 0; j < 16; ++j) accf[i * 16 + j] = fmaf(Af[rr + i][k], Bf[k][cc + j], accf[i * 16 + j]);
-    }
+        for (int j = 0; j < 16; ++j) accf[i * 16 + j] = fmaf(Af[rr + i][k], Bf[k][cc + j], accf[i * 16 + j]);
     __syncthreads();
   }
-  if (bf16) {
-    const int g = lane >> 2, t = lane & 3;
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 2; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const int r = m0 + wm + i * 16 + g + h * 8, c = n0 + wn + j * 8 + t * 2 + e;
-            if (r < M && c < N) C[(size_t)r * N + c] = acc[i][j][h * 2 + e] + (bias ? bias[c] : 0.0f);
-          }
-  } else {
-    const int rr = (tid >> 2) * 2, cc = (tid & 3) * 16;
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int r = m0 + rr + i, c = n0 + cc + j;
-        if (r < M && c < N) C[(size_t)r * N + c] = accf[i * 16 + j] + (bias ? bias[c] : 0.0f);
-      }
-  }
+    for (int j = 0; j < 16; ++j) {
+      const int r = m0 + rr + i, c = n0 + cc + j;
+      if (r < M && c < N) C[(size_t)r * N + c] = accf[i * 16 + j] + (bias ? bias[c] : 0.0f);
+    }
 }
 
 __device__ __forceinline__ float sig(float z) { return 1.0f / (1.0f + expf(-z)); }
@@ -226,11 +167,34 @@ __global__ void to_bf16_kernel(const float* p, __nv_bfloat16* pb, size_t n) {
     pb[i] = __float2bfloat16(p[i]);
 }
 
+// BF16: operands rounded to BF16, tcgen05 MMAs (Bb, when given, is the BF16
+// copy of B for tB == false); otherwise the FP32 kernel.  err: device flag.
 cudaError_t gemm(const float* A, const float* B, const __nv_bfloat16* Bb, float* C, const float* bias, int M, int N,
-                 int K, bool tA, bool tB, bool bf16, cudaStream_t s) {
+                 int K, bool tA, bool tB, bool bf16, int* err, cudaStream_t s) {
+  if (bf16) {
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBytes);
+    if (e != cudaSuccess) return e;
+    dim3 grid((N + kTcN - 1) / kTcN, (M + kTcM - 1) / kTcM);
+    tc_gemm_kernel<<<grid, kTcThreads, kTcSmemBytes, s>>>(A, B, tB ? nullptr : Bb, C, bias, M, N, K, tA, tB, err);
+    return cudaGetLastError();
+  }
   dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
-  gemm_kernel<<<grid, 128, 0, s>>>(A, B, Bb, C, bias, M, N, K, tA, tB, bf16);
+  gemm_kernel<<<grid, 128, 0, s>>>(A, B, C, bias, M, N, K, tA, tB);
   return cudaGetLastError();
+}
+
+// FSIM_ECUDA when a tensor-core GEMM since the last check gave up waiting for
+// its MMAs (the flag is cleared); synchronises the stream
+int tc_status(fsim_mlp* n, cudaStream_t s) {
+  int flag = 0;
+  FSIM_CK(cudaMemcpyAsync(&flag, n->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FSIM_CK(cudaStreamSynchronize(s));
+  if (flag) {
+    FSIM_CK(cudaMemset(n->tc_err, 0, sizeof(int)));
+    set_error("MLP GEMM: tensor-core MMAs did not complete");
+    return FSIM_ECUDA;
+  }
+  return FSIM_OK;
 }
 
 int ensure_batch(fsim_mlp* n, int b) {
@@ -253,11 +217,11 @@ int forward(fsim_mlp* n, const float* x, int b, bool bf16, cudaStream_t s) {
   const int w = n->width;
   const size_t bw = (size_t)b * w;
   const int th = 256, bl = (int)std::min<size_t>((bw + th - 1) / th, 1024);
-  FSIM_CK(gemm(x, n->p + o.W1, n->pb + o.W1, n->z1, n->p + o.b1, b, w, n->nin, false, false, bf16, s));
+  FSIM_CK(gemm(x, n->p + o.W1, n->pb + o.W1, n->z1, n->p + o.b1, b, w, n->nin, false, false, bf16, n->tc_err, s));
   silu_kernel<<<bl, th, 0, s>>>(n->z1, n->h1, bw);
-  FSIM_CK(gemm(n->h1, n->p + o.W2, n->pb + o.W2, n->z2, n->p + o.b2, b, w, w, false, false, bf16, s));
+  FSIM_CK(gemm(n->h1, n->p + o.W2, n->pb + o.W2, n->z2, n->p + o.b2, b, w, w, false, false, bf16, n->tc_err, s));
   silu_kernel<<<bl, th, 0, s>>>(n->z2, n->h2, bw);
-  FSIM_CK(gemm(n->h2, n->p + o.W3, n->pb + o.W3, n->y, n->p + o.b3, b, n->nout, w, false, false, bf16, s));
+  FSIM_CK(gemm(n->h2, n->p + o.W3, n->pb + o.W3, n->y, n->p + o.b3, b, n->nout, w, false, false, bf16, n->tc_err, s));
   return FSIM_OK;
 }
 
@@ -272,17 +236,17 @@ int backward(fsim_mlp* n, const float* x, const float* t, const float* mask, int
   loss_kernel<<<blocks(bo), th, 0, s>>>(n->y, t, mask, n->dy, n->scal, bo);
   scale_kernel<<<blocks(bo), th, 0, s>>>(n->dy, n->scal, bo);
   // layer 3
-  FSIM_CK(gemm(n->h2, n->dy, nullptr, n->g + o.W3, nullptr, w, n->nout, b, true, false, bf16, s));
+  FSIM_CK(gemm(n->h2, n->dy, nullptr, n->g + o.W3, nullptr, w, n->nout, b, true, false, bf16, n->tc_err, s));
   colsum_kernel<<<(n->nout + 127) / 128, 128, 0, s>>>(n->dy, n->g + o.b3, b, n->nout);
-  FSIM_CK(gemm(n->dy, n->p + o.W3, nullptr, n->d2, nullptr, b, w, n->nout, false, true, bf16, s));
+  FSIM_CK(gemm(n->dy, n->p + o.W3, nullptr, n->d2, nullptr, b, w, n->nout, false, true, bf16, n->tc_err, s));
   silu_back_kernel<<<blocks(bw), th, 0, s>>>(n->z2, n->d2, bw);
   // layer 2
-  FSIM_CK(gemm(n->h1, n->d2, nullptr, n->g + o.W2, nullptr, w, w, b, true, false, bf16, s));
+  FSIM_CK(gemm(n->h1, n->d2, nullptr, n->g + o.W2, nullptr, w, w, b, true, false, bf16, n->tc_err, s));
   colsum_kernel<<<(w + 127) / 128, 128, 0, s>>>(n->d2, n->g + o.b2, b, w);
-  FSIM_CK(gemm(n->d2, n->p + o.W2, nullptr, n->d1, nullptr, b, w, w, false, true, bf16, s));
+  FSIM_CK(gemm(n->d2, n->p + o.W2, nullptr, n->d1, nullptr, b, w, w, false, true, bf16, n->tc_err, s));
   silu_back_kernel<<<blocks(bw), th, 0, s>>>(n->z1, n->d1, bw);
   // layer 1
-  FSIM_CK(gemm(x, n->d1, nullptr, n->g + o.W1, nullptr, n->nin, w, b, true, false, bf16, s));
+  FSIM_CK(gemm(x, n->d1, nullptr, n->g + o.W1, nullptr, n->nin, w, b, true, false, bf16, n->tc_err, s));
   colsum_kernel<<<(w + 127) / 128, 128, 0, s>>>(n->d1, n->g + o.b1, b, w);
   return FSIM_OK;
 }
@@ -318,8 +282,11 @@ int fsim_mlp_create(int nin, int width, int nout, const float* init_params, fsim
   float** bufs[] = {&n->p, &n->g, &n->m, &n->v};
   for (float** q : bufs)
     if ((rc = dev_alloc(q, n->np)) != FSIM_OK) return fail(rc);
-  if ((rc = dev_alloc(&n->pb, n->np)) != FSIM_OK || (rc = dev_alloc(&n->scal, 2)) != FSIM_OK) return fail(rc);
+  if ((rc = dev_alloc(&n->pb, n->np)) != FSIM_OK || (rc = dev_alloc(&n->scal, 2)) != FSIM_OK ||
+      (rc = dev_alloc(&n->tc_err, 1)) != FSIM_OK)
+    return fail(rc);
   if (cudaMemcpy(n->p, init_params, sizeof(float) * n->np, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(n->tc_err, 0, sizeof(int)) != cudaSuccess ||
       cudaMemset(n->m, 0, sizeof(float) * n->np) != cudaSuccess ||
       cudaMemset(n->v, 0, sizeof(float) * n->np) != cudaSuccess) {
     set_error("fsim_mlp_create: upload failed");
@@ -337,6 +304,7 @@ void fsim_mlp_destroy(fsim_mlp* n) {
                     &n->scal};
   for (float** q : bufs) dev_free(*q);
   dev_free(n->pb);
+  dev_free(n->tc_err);
   delete n;
 }
 
@@ -413,7 +381,7 @@ int fsim_mlp_forward(fsim_mlp* n, const float* x, float* y, int batch, int bf16,
   FSIM_TRY(ensure_batch(n, batch));
   FSIM_TRY(forward(n, x, batch, bf16 != 0, s));
   FSIM_CK(cudaMemcpyAsync(y, n->y, sizeof(float) * batch * n->nout, cudaMemcpyDeviceToDevice, s));
-  return FSIM_OK;
+  return bf16 ? tc_status(n, s) : FSIM_OK;
 }
 
 int fsim_mlp_grad(fsim_mlp* n, const float* x, const float* t, const float* mask, int batch, int bf16, float* loss,
@@ -431,7 +399,7 @@ int fsim_mlp_grad(fsim_mlp* n, const float* x, const float* t, const float* mask
   if (grad_host) FSIM_CK(cudaMemcpyAsync(grad_host, n->g, sizeof(float) * n->np, cudaMemcpyDeviceToHost, s));
   FSIM_CK(cudaStreamSynchronize(s));
   if (loss) *loss = sc[0] / std::max(sc[1], 1.0f);
-  return FSIM_OK;
+  return bf16 ? tc_status(n, s) : FSIM_OK;
 }
 
 int fsim_mlp_adam_step(fsim_mlp* n, const float* grad_host, float lr, void* stream) {
@@ -471,7 +439,7 @@ int fsim_mlp_train_step(fsim_mlp* n, const float* x, const float* t, const float
     FSIM_CK(cudaStreamSynchronize(s));
     *loss = sc[0] / std::max(sc[1], 1.0f);
   }
-  return FSIM_OK;
+  return tc_status(n, s);
 }
 
 }  // extern "C"

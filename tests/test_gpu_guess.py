@@ -54,6 +54,44 @@ def test_mlp_forward_and_gradient_match_fp64_oracle():
     assert np.linalg.norm(gb - go) / np.linalg.norm(go) < 5e-2
 
 
+def _bf16(a):
+    """Round FP32 values to BF16 (round to nearest even), kept as FP32."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32)
+
+
+@pytest.mark.parametrize("width", [32, 256])
+def test_mlp_bf16_forward_is_the_bf16_operand_product(width):
+    # the BF16 forward pass is the network with every GEMM operand rounded to
+    # BF16 and products accumulated in FP32 (tensor cores): against that
+    # definition in FP64 it agrees to accumulation order and rare one-ulp BF16
+    # differences of the FP32-computed activations; batch 300 spans three
+    # 128-row tiles, width 256 four 64-wide K chunks, 225 outputs two column tiles
+    net, x, t, m = _net_and_data(width=width)
+    p = net.params().astype(np.float32)
+    nin, nout, w = 48, 225, width
+    sizes = [nin * w, w, w * w, w, w * nout, nout]
+    parts = np.split(p, np.cumsum(sizes)[:-1])
+    W1, b1, W2, b2, W3, b3 = (parts[0].reshape(nin, w), parts[1], parts[2].reshape(w, w), parts[3],
+                              parts[4].reshape(w, nout), parts[5])
+
+    def lin(h, W, b):
+        return _bf16(h).astype(np.float64) @ _bf16(W).astype(np.float64) + b
+
+    def silu(z):
+        return z / (1.0 + np.exp(-z))
+
+    h1 = silu(lin(x, W1, b1)).astype(np.float32)
+    h2 = silu(lin(h1, W2, b2)).astype(np.float32)
+    yref = lin(h2, W3, b3)
+    xd = torch.from_numpy(x).cuda()
+    y = torch.empty((x.shape[0], nout), dtype=torch.float32, device="cuda")
+    net.forward(xd.data_ptr(), y.data_ptr(), x.shape[0], bf16=True)
+    torch.cuda.synchronize()
+    assert np.abs(y.cpu().numpy() - yref).max() < 2e-3 * np.abs(yref).max()
+
+
 def test_training_reduces_loss():
     from paper_2510_24968_gb300.guess import train
     net, x, t, m = _net_and_data(width=64, b=512, seed=1)
