@@ -314,8 +314,7 @@ typedef struct {
   int mixed_fallback;   /* 1: FSIM_MIXED was requested, but the overlap's smallest eigenvalue is below
                            FSIM_MIXED_MIN_S_EIG: in so nearly linearly dependent a basis the density has
                            large elements, and FP32 integral errors multiplied by them exceed the mixed
-                           path's 1e-6 Eh bound, so every build ran FP64-accurate (FSIM_DFLOAT when
-                           final_fp64 = 2, else FSIM_FP64) */
+                           path's 1e-6 Eh bound, so every build ran in FSIM_FP64 */
 } fsim_scf_result;
 
 /* Smallest overlap eigenvalue for which fsim_scf / fsim_scf_batched run FSIM_MIXED builds. */

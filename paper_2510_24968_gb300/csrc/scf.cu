@@ -389,9 +389,12 @@ int fsim_scf(fsim_basis* b, const fsim_scf_opts* opts, fsim_scf_result* res) {
   const bool mixed_req = o.fock.precision == FSIM_MIXED;
   const bool mixed = mixed_req && smin >= FSIM_MIXED_MIN_S_EIG;
   res->mixed_fallback = mixed_req && !mixed;
-  // precision of the FP64-accurate builds: the requested one, or on the mixed
-  // path the resets' (FP64, or double-float with final_fp64 == 2)
-  const int prec64 = !mixed_req ? o.fock.precision : (o.final_fp64 == 2 ? FSIM_DFLOAT : FSIM_FP64);
+  // precision of the FP64-accurate builds: the requested one; on the mixed path
+  // the resets' (FP64, or double-float with final_fp64 == 2); FP64 for a mixed
+  // request refused by the overlap bound, since a basis that near dependent
+  // amplifies double-float's 2^-47 rounding of the integrals as well
+  const int prec64 = !mixed_req ? o.fock.precision
+                                : (mixed && o.final_fp64 == 2 ? FSIM_DFLOAT : FSIM_FP64);
   // phase 0: mixed settling; phase 2: final accuracy.  With final_fp64 each
   // FP64 build resets G; the iteration only stops once the density has not
   // moved (rms 1e-6) since the last reset, so the FP32 part of G is tiny.
