@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(kTcThreads) tc_gemm_kernel(const float* __rest
       asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
       for (int kk = 0; kk < kTcK / 16; ++kk) {
+        if (k0 + kk * 16 >= K) break;  // the zero padding past K needs no MMA (kk = 0 always runs)
         const uint64_t ad = tc_desc(aS + (uint32_t)kk * 256u, kTcLbo, kTcSbo);
         const uint64_t bd = tc_desc(bS + (uint32_t)kk * 256u, kTcLbo, kTcSbo);
         const uint32_t accum = (c > 0 || kk > 0) ? 1u : 0u;
