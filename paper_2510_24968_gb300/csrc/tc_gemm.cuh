@@ -33,7 +33,7 @@ static_assert(4 * kTcSmemBytes > 227 * 1024, "four CTAs per SM would oversubscri
 // (row / 8, k / 8) at ((row / 8) * 8 + k / 8) * 128, row % 8 at 16-byte steps,
 // k % 8 at 2-byte steps.  K-adjacent core matrices are 128 B apart, row groups
 // 1024 B apart.
-__device__ __forceinline__ uint32_t tc_off(int row, int k) {
+__host__ __device__ __forceinline__ uint32_t tc_off(int row, int k) {
   return ((uint32_t)(((row >> 3) * (kTcK / 8) + (k >> 3)) << 7)) + ((uint32_t)(row & 7) << 4) +
          ((uint32_t)(k & 7) << 1);
 }
@@ -43,7 +43,7 @@ constexpr uint32_t kTcLbo = 128, kTcSbo = 1024;  // K-adjacent core matrices, 8-
 // shared-memory matrix descriptor: start address, leading-dimension byte offset
 // (between K-adjacent core matrices), stride-dimension byte offset (between
 // 8-row groups), descriptor version 1, no swizzle
-__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+__host__ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
